@@ -1,0 +1,188 @@
+/*
+ * dd.h -- C ABI of the GB300 (sm_103a) dedispersion + single-pulse-search library.
+ *
+ * The operations follow the problem statement of Novotny, Adamek & Armour,
+ * "Implementing CUDA Streams into AstroAccelerate -- A Case Study":
+ *   - Sec. 1 (time chunking over CUDA streams) and Sec. 2 (pinned memory, asynchronous copies,
+ *     stream IDs, no implicit synchronisation in the compute loop);
+ *   - Sec. 2.1 (the dedispersion phase, streamed);
+ *   - Sec. 2.2 (the single-pulse-search phase; all allocation moved to the planning phase);
+ *   - Sec. 3 (the DM-trial plan: ~6000 trials over 0-3000 pc cm^-3, SKA-like input).
+ * The paper prints no formulas. The readings used here:
+ *   delay      s[i][c] = floor(k_DM*DM_i*(f_c^-2 - f_ref^-2) / (tsamp*d) + 0.5),
+ *              k_DM = 4.148808e3 s MHz^2 pc^-1 cm^3, f_ref = max f_c, DM_i = dm_start + i*dm_step
+ *   decimation x_d[c][m] = sum_{k<d} x[c][m*d + k]   (windows aligned at global sample 0)
+ *   dedisp.    y[i][j]  = sum_c x_d[c][j + s[i][c]]   (exact integer sum, int32)
+ *   search     trailing boxcars B_w[j] (w decimated samples), SNR = (n*B - w*S1) /
+ *              (sqrt(w)*sqrt(n*S2 - S1^2)) over the chunk window's own moments, one candidate
+ *              per aligned block of `peak_block` samples (max over samples and widths; ties go to
+ *              the earlier sample, then the narrower width) when SNR >= threshold.
+ *
+ * Conventions
+ *   - Every function returns DD_OK (0) or a negative DD_ERR_* code; dd_last_error() gives a
+ *     message for the calling thread's last failure.
+ *   - All device and pinned host memory is allocated in dd_plan (Sec. 2.2: allocation moved out of
+ *     the compute phase) and released by dd_plan_destroy. dd_run / sps_run / dd_candidates
+ *     allocate nothing.
+ *   - A plan is used from one host thread at a time.
+ *   - Layouts: filterbank chunks are time-major uint8, x[t][c] (row = one spectrum of nchans
+ *     bytes, channel 0 first). Series are int32 [trial][sample] of one range.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DD_OK 0
+#define DD_ERR_ARG (-1)     /* invalid argument or plan parameter */
+#define DD_ERR_NOMEM (-2)   /* device or pinned host allocation failed in dd_plan */
+#define DD_ERR_CUDA (-3)    /* a CUDA runtime call or kernel failed */
+#define DD_ERR_TIMEOUT (-4) /* a bounded wait for the GPU ran out */
+#define DD_ERR_CAP (-5)     /* more candidates than the buffer holds; *ncands = the true count */
+#define DD_ERR_STATE (-6)   /* call out of order (e.g. candidates of a chunk already recycled) */
+
+/* Plan option flags. */
+#define DD_FLAG_TIMING 1u   /* bracket every dedispersion launch with CUDA events (dd_stats) */
+#define DD_FLAG_NAIVE 2u    /* use the one-thread-per-output dedispersion kernel (testing aid) */
+
+typedef struct dd_plan_s* dd_plan_t;
+
+/* One DM range of the trial plan (Sec. 3): trials dm_start + i*dm_step, i < n_trials, searched
+ * on data decimated by `decimation` (a power of two, 1..256). */
+typedef struct {
+  double dm_start;
+  double dm_step;
+  int32_t n_trials;
+  int32_t decimation;
+} dd_range_t;
+
+typedef struct {
+  int64_t chunk_len;   /* most new samples one dd_run call may deliver (Sec. 1: a time chunk);
+                          a multiple of 256 */
+  int32_t n_streams;   /* CUDA streams the chunks rotate over (Sec. 2: stream IDs), 1..16 */
+  int32_t max_width;   /* largest boxcar width (original samples) sps_run will be given */
+  int32_t peak_block;  /* samples per candidate block (decimated samples of each range), >= 1 */
+  int32_t device;      /* CUDA device ordinal */
+  int64_t max_cands;   /* device candidate buffer per chunk; 0 = default (1<<20) */
+  uint32_t flags;      /* DD_FLAG_* */
+  int32_t reserved;
+} dd_opts_t;
+
+/* One single-pulse candidate (Sec. 2.2). */
+typedef struct {
+  int32_t trial;   /* trial index within its range */
+  int32_t range;   /* range index in the plan */
+  int64_t t_start; /* first original sample of the boxcar, counted from the first sample ever
+                      given to dd_run */
+  int32_t width;   /* boxcar width in original samples */
+  int32_t pad;
+  double snr;      /* FP64 SNR */
+} dd_cand_t;
+
+/*
+ * dd_plan -- build a plan (Sec. 1 "mapping of tasks ... allocation of all necessary memory";
+ * Sec. 3 DM plan).
+ *   freqs_mhz : host [nchans] channel-centre frequencies in MHz (any order; f_ref = the largest)
+ *   tsamp_s   : sample time in seconds (> 0)
+ *   ranges    : host [nranges] DM ranges; n_trials >= 1; decimation a power of two <= 256
+ *   opts      : host, see dd_opts_t
+ *   out       : receives the plan handle (owned by the caller, release with dd_plan_destroy)
+ * Builds the delay table on the GPU, derives the overlap O (original samples of history every
+ * chunk needs: the largest delay of any range, rounded up to the largest decimation), creates
+ * n_streams CUDA streams and allocates every device and pinned buffer used later.
+ * Errors: DD_ERR_ARG (bad sizes, nchans*255*max(width, decimation) >= 2^31, delays beyond
+ * int32), DD_ERR_NOMEM, DD_ERR_CUDA.
+ */
+int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_range_t* ranges,
+            int32_t nranges, const dd_opts_t* opts, dd_plan_t* out);
+
+/*
+ * dd_plan_info -- plan facts.
+ *   overlap  : O in original samples (may be NULL)
+ *   ntrials  : total trials over all ranges (may be NULL)
+ *   shifts   : receives a plan-owned HOST pointer to the delay table, int32
+ *              [sum_r n_trials_r][nchans], ranges in plan order, valid until dd_plan_destroy
+ *              (may be NULL)
+ */
+int dd_plan_info(dd_plan_t plan, int64_t* overlap, int32_t* ntrials, const int32_t** shifts);
+
+/*
+ * dd_run -- enqueue the dedispersion of the next time chunk (Sec. 1, Sec. 2.1).
+ *   chunk       : time-major uint8 [nsamp][nchans]; a host pointer (pinned memory gives
+ *                 asynchronous copies, Sec. 2.1) or a device pointer. Read-only; it must stay
+ *                 valid and unchanged until this chunk's dd_candidates returns or dd_sync.
+ *   nsamp       : new samples, 0 < nsamp <= chunk_len, a multiple of the largest decimation
+ *   cuda_stream : NULL = the plan's own streams (chunk k runs on stream k mod n_streams);
+ *                 otherwise every stage of this chunk is enqueued on that cudaStream_t.
+ * The plan keeps O samples of history on the device, so consecutive chunks dedisperse exactly
+ * like one long input. After the chunk, the outputs of range r are the global decimated indices
+ * j with j*d_r in [max(0, T-O), max(0, T+nsamp-O)), T = samples delivered before this chunk.
+ * Returns immediately (asynchronous). The chunk is numbered 0, 1, 2, ... in call order;
+ * its results stay available until n_streams further chunks have been run.
+ * Errors: DD_ERR_ARG, DD_ERR_CUDA.
+ */
+int dd_run(dd_plan_t plan, const uint8_t* chunk, int64_t nsamp, void* cuda_stream);
+
+/*
+ * dd_series -- device view of the most recent chunk's dedispersed series of one range.
+ *   dev_ptr : receives a plan-owned DEVICE pointer to int32 [n_trials_r][stride]
+ *   len     : samples of the chunk window (row j = global decimated index *j0 + j)
+ *   stride  : row stride in elements;  j0 : global decimated index of sample 0 (may be NULL)
+ * The data is complete once the chunk's stream has finished (dd_sync or dd_candidates).
+ */
+int dd_series(dd_plan_t plan, int32_t range, const int32_t** dev_ptr, int64_t* len,
+              int64_t* stride, int64_t* j0);
+
+/*
+ * sps_run -- enqueue the single pulse search of the most recent chunk (Sec. 2.2).
+ *   widths    : host [nwidths] boxcar widths in original samples, strictly increasing,
+ *               1 <= w <= max_width. Range r searches the widths w with w >= d_r and
+ *               w % d_r == 0, as w/d_r decimated samples.
+ *   threshold : candidates have SNR >= threshold
+ * Enqueued on the chunk's own stream after its dedispersion (stream-ordered; no cross-stream
+ * wait on atomics). Asynchronous; collect the result with dd_candidates.
+ * Errors: DD_ERR_ARG, DD_ERR_STATE (no chunk, or already searched), DD_ERR_CUDA.
+ */
+int sps_run(dd_plan_t plan, const int32_t* widths, int32_t nwidths, float threshold);
+
+/*
+ * dd_candidates -- wait for chunk `seq`'s search and copy its candidates.
+ *   seq    : chunk number (0-based dd_run call count); must be one of the last n_streams chunks
+ *   out    : caller-owned host array of cap entries, sorted by (range, trial, t_start, width)
+ *   ncands : receives the number of candidates found
+ *   timeout_ms : bound on the wait (<= 0: 600000)
+ * Errors: DD_ERR_STATE (unknown, recycled or unsearched chunk), DD_ERR_TIMEOUT, DD_ERR_CAP
+ * (more than cap or than opts.max_cands; *ncands holds the true count, out holds the first cap
+ * found in sorted order of those kept), DD_ERR_CUDA.
+ */
+int dd_candidates(dd_plan_t plan, int64_t seq, dd_cand_t* out, int64_t cap, int64_t* ncands,
+                  int64_t timeout_ms);
+
+/* dd_sync -- wait for all enqueued work of the plan. Errors: DD_ERR_CUDA. */
+int dd_sync(dd_plan_t plan);
+
+/*
+ * dd_stats -- counters of the plan since creation or the last reset.
+ *   launches      : kernels launched by the plan
+ *   dedisp_ms     : summed device time of the dedispersion launches (needs DD_FLAG_TIMING;
+ *                   measured with CUDA events on the launching stream; complete after dd_sync)
+ *   dedisp_launches : dedispersion launches timed
+ *   reset         : non-zero = zero the counters after reading
+ */
+int dd_stats(dd_plan_t plan, int64_t* launches, double* dedisp_ms, int64_t* dedisp_launches,
+             int32_t reset);
+
+/* dd_plan_destroy -- wait for the plan's work and free everything it allocated. NULL is a no-op. */
+void dd_plan_destroy(dd_plan_t plan);
+
+/* dd_last_error -- message of the calling thread's last error ("" if none). Library-owned. */
+const char* dd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_H */

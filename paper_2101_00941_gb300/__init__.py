@@ -1,0 +1,232 @@
+"""Python binding of the GB300 dedispersion + single-pulse-search library (``libdd.so``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels behind the C ABI declared in ``include/dd.h``. The functions keep the C
+names (``dd_plan``, ``dd_run``, ``sps_run``, ...); ``Plan`` is a thin owner of a
+plan handle. There is no CPU fallback: if the library was not built, loading
+it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build_lib import LIB_PATH, build  # noqa: F401
+
+DD_OK = 0
+DD_ERR_ARG = -1
+DD_ERR_NOMEM = -2
+DD_ERR_CUDA = -3
+DD_ERR_TIMEOUT = -4
+DD_ERR_CAP = -5
+DD_ERR_STATE = -6
+DD_FLAG_TIMING = 1
+DD_FLAG_NAIVE = 2
+
+EXPORTS = ("dd_plan", "dd_plan_info", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
+           "dd_stats", "dd_plan_destroy", "dd_last_error")
+
+
+class dd_range_t(ctypes.Structure):
+    _fields_ = [("dm_start", ctypes.c_double), ("dm_step", ctypes.c_double),
+                ("n_trials", ctypes.c_int32), ("decimation", ctypes.c_int32)]
+
+
+class dd_opts_t(ctypes.Structure):
+    _fields_ = [("chunk_len", ctypes.c_int64), ("n_streams", ctypes.c_int32),
+                ("max_width", ctypes.c_int32), ("peak_block", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("max_cands", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+CAND_DTYPE = np.dtype([("trial", "<i4"), ("range", "<i4"), ("t_start", "<i8"), ("width", "<i4"),
+                       ("pad", "<i4"), ("snr", "<f8")])
+
+
+class DDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2101_00941_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f32, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                                  ctypes.c_double)
+        P = ctypes.POINTER
+        L.dd_plan.argtypes = [vp, i32, f64, vp, i32, P(dd_opts_t), P(vp)]
+        L.dd_plan_info.argtypes = [vp, P(i64), P(i32), P(vp)]
+        L.dd_run.argtypes = [vp, vp, i64, vp]
+        L.dd_series.argtypes = [vp, i32, P(vp), P(i64), P(i64), P(i64)]
+        L.sps_run.argtypes = [vp, vp, i32, f32]
+        L.dd_candidates.argtypes = [vp, i64, vp, i64, P(i64), i64]
+        L.dd_sync.argtypes = [vp]
+        L.dd_stats.argtypes = [vp, P(i64), P(f64), P(i64), i32]
+        L.dd_plan_destroy.argtypes = [vp]
+        L.dd_plan_destroy.restype = None
+        L.dd_last_error.argtypes = []
+        L.dd_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS[:-2]:
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def dd_last_error() -> str:
+    return lib().dd_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != DD_OK:
+        raise DDError(rc, dd_last_error())
+    return rc
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array, a torch tensor (host or device) or an int."""
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def dd_plan(freqs_mhz, tsamp_s: float, ranges, chunk_len: int, n_streams: int = 1,
+            max_width: int = 256, peak_block: int = 32, device: int = 0, max_cands: int = 0,
+            flags: int = 0) -> int:
+    """Create a plan; ``ranges`` rows are (dm_start, dm_step, n_trials, decimation)."""
+    f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+    rr = (dd_range_t * len(ranges))(*[dd_range_t(float(r[0]), float(r[1]), int(r[2]), int(r[3]))
+                                      for r in ranges])
+    o = dd_opts_t(int(chunk_len), int(n_streams), int(max_width), int(peak_block), int(device),
+                  int(max_cands), int(flags), 0)
+    h = ctypes.c_void_p()
+    _check(lib().dd_plan(f.ctypes.data, f.size, float(tsamp_s), ctypes.addressof(rr), len(ranges),
+                         ctypes.byref(o), ctypes.byref(h)))
+    return h.value
+
+
+def dd_plan_info(plan: int, nchans: int):
+    """(overlap, total trials, host copy of the delay table [trials][nchans])."""
+    O = ctypes.c_int64()
+    nt = ctypes.c_int32()
+    sp = ctypes.c_void_p()
+    _check(lib().dd_plan_info(plan, ctypes.byref(O), ctypes.byref(nt), ctypes.byref(sp)))
+    buf = (ctypes.c_int32 * (nt.value * nchans)).from_address(sp.value)
+    return O.value, nt.value, np.ctypeslib.as_array(buf).reshape(nt.value, nchans).copy()
+
+
+def dd_run(plan: int, chunk, nsamp: int, cuda_stream: int = 0):
+    _check(lib().dd_run(plan, _ptr(chunk), int(nsamp), int(cuda_stream) or None))
+
+
+def dd_series(plan: int, range_idx: int):
+    """(device pointer, window length, row stride, global index of sample 0)."""
+    p = ctypes.c_void_p()
+    n, st, j0 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().dd_series(plan, int(range_idx), ctypes.byref(p), ctypes.byref(n),
+                           ctypes.byref(st), ctypes.byref(j0)))
+    return p.value, n.value, st.value, j0.value
+
+
+def sps_run(plan: int, widths, threshold: float):
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    _check(lib().sps_run(plan, w.ctypes.data, w.size, ctypes.c_float(threshold)))
+
+
+def dd_candidates(plan: int, seq: int, cap: int = 1 << 20, timeout_ms: int = 0) -> np.ndarray:
+    out = np.zeros(cap, dtype=CAND_DTYPE)
+    n = ctypes.c_int64()
+    rc = lib().dd_candidates(plan, int(seq), out.ctypes.data, int(cap), ctypes.byref(n),
+                             int(timeout_ms))
+    _check(rc)
+    return out[:n.value]
+
+
+def dd_sync(plan: int):
+    _check(lib().dd_sync(plan))
+
+
+def dd_stats(plan: int, reset: bool = False):
+    """(kernel launches, summed dedispersion ms, dedispersion launches timed)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().dd_stats(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(reset)))
+    return a.value, b.value, c.value
+
+
+def dd_plan_destroy(plan: int):
+    if plan:
+        lib().dd_plan_destroy(plan)
+
+
+class Plan:
+    """Owner of a plan handle (destroys it on close)."""
+
+    def __init__(self, freqs_mhz, tsamp_s, ranges, chunk_len, **kw):
+        self.nchans = int(np.asarray(freqs_mhz).size)
+        self.ranges = [tuple(r) for r in ranges]
+        self.h = dd_plan(freqs_mhz, tsamp_s, ranges, chunk_len, **kw)
+        self.O, self.ntrials, self.shifts = dd_plan_info(self.h, self.nchans)
+        self.seq = -1
+
+    def run(self, chunk, nsamp=None, cuda_stream=0) -> int:
+        n = chunk.shape[0] if nsamp is None else nsamp
+        dd_run(self.h, chunk, n, cuda_stream)
+        self.seq += 1
+        return self.seq
+
+    def search(self, widths, threshold):
+        sps_run(self.h, widths, threshold)
+
+    def candidates(self, seq=None, cap=1 << 20, timeout_ms=0):
+        return dd_candidates(self.h, self.seq if seq is None else seq, cap, timeout_ms)
+
+    def series(self, range_idx):
+        """The latest chunk's series of a range: (torch int32 [n_trials][len] copy, j0)."""
+        ptr, n, stride, j0 = dd_series(self.h, range_idx)
+        ntr = int(self.ranges[range_idx][2])
+        dd_sync(self.h)
+        return device_view(ptr, (ntr, stride), "<i4")[:, :n].clone(), j0
+
+    def sync(self):
+        dd_sync(self.h)
+
+    def stats(self, reset=False):
+        return dd_stats(self.h, reset)
+
+    def close(self):
+        if self.h:
+            dd_plan_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _CudaArray:
+    """Exposes a plan-owned device buffer through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, typestr: str):
+    """A torch tensor viewing device memory owned by the library (valid while the plan lives)."""
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")

@@ -1,0 +1,619 @@
+// C ABI of the library: planning, the chunk/stream scheduler and the search driver.
+//
+// Scheduler (Sec. 1 and Sec. 2 of the paper: time chunks, stream IDs, pinned memory,
+// asynchronous copies, no allocation or implicit synchronisation in the compute loop):
+//   chunk k runs on slot k mod n_streams, each slot owning a CUDA stream and its own device
+//   buffers (staging, channel-major ring, decimated rings, series, moments, candidates).
+//   The history a chunk needs (the last H >= O samples of the stream so far) lives on the
+//   device in `hist`; chunk k loads it after chunk k-1 saved it (one event per plan), so the
+//   only cross-stream dependency is this short device-to-device copy.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dd_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define DD_CK(call)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(DD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+  } while (0)
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+// Bounded wait on an event (no spin on the GPU side; host polls with a deadline).
+int wait_event(cudaEvent_t ev, int64_t timeout_ms) {
+  if (timeout_ms <= 0) timeout_ms = 600000;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return DD_OK;
+    if (e != cudaErrorNotReady)
+      return fail(DD_ERR_CUDA, "event wait failed: %s", cudaGetErrorString(e));
+    const auto dt = std::chrono::steady_clock::now() - t0;
+    if (std::chrono::duration_cast<std::chrono::milliseconds>(dt).count() > timeout_ms)
+      return fail(DD_ERR_TIMEOUT, "GPU work did not finish within %lld ms",
+                  (long long)timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaStream_t used = nullptr;  // stream the current chunk was enqueued on
+  uint8_t* staging = nullptr;   // [chunk_len][nchans] host-input landing buffer
+  uint8_t* ring1 = nullptr;     // [C4][R1] channel-major, column 0 = global sample T - H
+  uint16_t* ringd[9] = {};      // level l >= 1 (decimation 2^l): [C4][Rd[l]]
+  int32_t* series = nullptr;    // every range, at series_off[r]
+  ddk::Moments* mom = nullptr;  // [total trials]
+  dd_cand_t* cands = nullptr;   // [max_cands]
+  unsigned long long* d_count = nullptr;
+  unsigned long long* h_count = nullptr;  // pinned
+  cudaEvent_t ev_free = nullptr;          // last work enqueued for this slot
+  cudaEvent_t ev_sps = nullptr;           // search + count readback done
+  int64_t seq = -1, T = 0, n = 0, lo = 0, hi = 0;
+  bool searched = false;
+};
+
+}  // namespace
+
+struct dd_plan_s {
+  int device = 0;
+  int32_t C = 0, C4 = 0;
+  double tsamp = 0;
+  std::vector<dd_range_t> ranges;
+  dd_opts_t opts{};
+  std::vector<int32_t> row0;       // first shift-table row of each range
+  int32_t total_rows = 0;
+  std::vector<int32_t> h_shifts;   // [total_rows][C] (plan_info view)
+  int32_t* d_shifts = nullptr;     // [total_rows][C4]
+  int64_t O = 0, H = 0, L = 0;
+  int dmax = 1, levels = 0;
+  int64_t R1 = 0;
+  int64_t Rd[9] = {};
+  std::vector<int64_t> series_off, series_stride;
+  int64_t series_elems = 0;
+  uint8_t* hist = nullptr;         // [C4][H] device history
+  cudaEvent_t ev_hist = nullptr;
+  std::vector<Slot> slots;
+  cudaStream_t io = nullptr;
+  cudaEvent_t ev_io = nullptr;
+  dd_cand_t* h_cands = nullptr;    // pinned [max_cands]
+  int64_t next_seq = 0, T_total = 0;
+  int64_t launches = 0;
+  // dedispersion timing (DD_FLAG_TIMING)
+  std::vector<cudaEvent_t> tev;
+  int64_t tev_used = 0;
+  double dedisp_ms = 0;
+  int64_t dedisp_launches = 0;
+};
+
+namespace {
+
+void free_plan(dd_plan_s* p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  for (auto& s : p->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+  }
+  if (p->io) cudaStreamSynchronize(p->io);
+  for (auto& s : p->slots) {
+    cudaFree(s.staging);
+    cudaFree(s.ring1);
+    for (auto* r : s.ringd) cudaFree(r);
+    cudaFree(s.series);
+    cudaFree(s.mom);
+    cudaFree(s.cands);
+    cudaFree(s.d_count);
+    cudaFreeHost(s.h_count);
+    if (s.ev_free) cudaEventDestroy(s.ev_free);
+    if (s.ev_sps) cudaEventDestroy(s.ev_sps);
+    if (s.stream) cudaStreamDestroy(s.stream);
+  }
+  for (auto e : p->tev) cudaEventDestroy(e);
+  cudaFree(p->d_shifts);
+  cudaFree(p->hist);
+  cudaFreeHost(p->h_cands);
+  if (p->ev_hist) cudaEventDestroy(p->ev_hist);
+  if (p->ev_io) cudaEventDestroy(p->ev_io);
+  if (p->io) cudaStreamDestroy(p->io);
+  delete p;
+}
+
+template <typename T>
+int dalloc(T** ptr, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc((void**)ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(DD_ERR_NOMEM, "device allocation of %zu bytes for %s failed", bytes, what);
+  }
+  return DD_OK;
+}
+
+// Harvest finished timing event pairs into the running total (all of them if `all`).
+int harvest_timing(dd_plan_s* p, bool all) {
+  for (int64_t k = 0; k < p->tev_used; ++k) {
+    cudaEvent_t a = p->tev[2 * k], b = p->tev[2 * k + 1];
+    if (all) {
+      DD_CK(cudaEventSynchronize(b));
+    }
+    float ms = 0;
+    DD_CK(cudaEventElapsedTime(&ms, a, b));
+    p->dedisp_ms += ms;
+    p->dedisp_launches += 1;
+  }
+  p->tev_used = 0;
+  return DD_OK;
+}
+
+int timing_begin(dd_plan_s* p, cudaStream_t st, int64_t* slot) {
+  *slot = -1;
+  if (!(p->opts.flags & DD_FLAG_TIMING)) return DD_OK;
+  if (2 * (p->tev_used + 1) > (int64_t)p->tev.size()) {
+    int rc = harvest_timing(p, true);
+    if (rc) return rc;
+  }
+  *slot = p->tev_used++;
+  DD_CK(cudaEventRecord(p->tev[2 * *slot], st));
+  return DD_OK;
+}
+
+int timing_end(dd_plan_s* p, cudaStream_t st, int64_t slot) {
+  if (slot < 0) return DD_OK;
+  DD_CK(cudaEventRecord(p->tev[2 * slot + 1], st));
+  return DD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dd_last_error(void) { return g_err.c_str(); }
+
+int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_range_t* ranges,
+            int32_t nranges, const dd_opts_t* opts, dd_plan_t* out) {
+  if (!out) return fail(DD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!freqs_mhz || !ranges || !opts) return fail(DD_ERR_ARG, "NULL argument");
+  if (nchans < 1 || nchans > 65532) return fail(DD_ERR_ARG, "nchans %d outside 1..65532", nchans);
+  if (!(tsamp_s > 0) || !std::isfinite(tsamp_s)) return fail(DD_ERR_ARG, "tsamp must be > 0");
+  if (nranges < 1 || nranges > ddk::kMaxRanges)
+    return fail(DD_ERR_ARG, "nranges %d outside 1..%d", nranges, ddk::kMaxRanges);
+  for (int c = 0; c < nchans; ++c)
+    if (!(freqs_mhz[c] > 0) || !std::isfinite(freqs_mhz[c]))
+      return fail(DD_ERR_ARG, "frequency %d is not a positive finite number", c);
+  int dmax = 1;
+  int64_t total_rows = 0;
+  for (int r = 0; r < nranges; ++r) {
+    const dd_range_t& R = ranges[r];
+    if (R.n_trials < 1 || R.n_trials > 65535)
+      return fail(DD_ERR_ARG, "range %d: n_trials %d outside 1..65535", r, R.n_trials);
+    if (!is_pow2(R.decimation) || R.decimation > 256)
+      return fail(DD_ERR_ARG, "range %d: decimation %d is not a power of two <= 256", r,
+                  R.decimation);
+    if (!(R.dm_start >= 0) || !(R.dm_step >= 0) || !std::isfinite(R.dm_start) ||
+        !std::isfinite(R.dm_step))
+      return fail(DD_ERR_ARG, "range %d: dm_start and dm_step must be finite and >= 0", r);
+    dmax = std::max(dmax, R.decimation);
+    total_rows += R.n_trials;
+  }
+  if (total_rows > (1 << 24)) return fail(DD_ERR_ARG, "too many trials");
+  const dd_opts_t& o = *opts;
+  if (o.chunk_len < 256 || o.chunk_len % 256 != 0 || o.chunk_len > (int64_t(1) << 31))
+    return fail(DD_ERR_ARG, "chunk_len %lld must be a positive multiple of 256",
+                (long long)o.chunk_len);
+  if (o.n_streams < 1 || o.n_streams > 16)
+    return fail(DD_ERR_ARG, "n_streams %d outside 1..16", o.n_streams);
+  if (o.max_width < 1 || o.max_width > 1024)
+    return fail(DD_ERR_ARG, "max_width %d outside 1..1024", o.max_width);
+  if (!is_pow2(o.peak_block) || o.peak_block > 32)
+    return fail(DD_ERR_ARG, "peak_block %d must be a power of two <= 32", o.peak_block);
+  if ((int64_t)nchans * 255 * std::max(dmax, o.max_width) >= (int64_t(1) << 31))
+    return fail(DD_ERR_ARG, "nchans*255*max(width, decimation) must be < 2^31 (int32 sums)");
+  if (o.max_cands < 0) return fail(DD_ERR_ARG, "max_cands < 0");
+
+  int ndev = 0;
+  DD_CK(cudaGetDeviceCount(&ndev));
+  if (o.device < 0 || o.device >= ndev)
+    return fail(DD_ERR_ARG, "device %d not present (%d devices)", o.device, ndev);
+  DD_CK(cudaSetDevice(o.device));
+
+  dd_plan_s* p = new dd_plan_s();
+  p->device = o.device;
+  p->C = nchans;
+  p->C4 = (int32_t)round_up(nchans, 4);
+  p->tsamp = tsamp_s;
+  p->ranges.assign(ranges, ranges + nranges);
+  p->opts = o;
+  if (p->opts.max_cands == 0) p->opts.max_cands = int64_t(1) << 20;
+  p->total_rows = (int32_t)total_rows;
+  p->dmax = dmax;
+  p->levels = ilog2(dmax);
+  p->L = o.chunk_len;
+  int rc = DD_OK;
+#define DD_TRY(x)          \
+  do {                     \
+    rc = (x);              \
+    if (rc) {              \
+      free_plan(p);        \
+      return rc;           \
+    }                      \
+  } while (0)
+#define DD_TRYCK(call)                                                             \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      free_plan(p);                                                                \
+      return fail(DD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    }                                                                              \
+  } while (0)
+
+  // ---- delay table on the GPU (plan phase: one-off)
+  std::vector<ddk::ShiftRange> sr(nranges);
+  p->row0.resize(nranges);
+  int32_t row = 0;
+  for (int r = 0; r < nranges; ++r) {
+    sr[r] = {ranges[r].dm_start, ranges[r].dm_step, ranges[r].n_trials, ranges[r].decimation,
+             row, 0};
+    p->row0[r] = row;
+    row += ranges[r].n_trials;
+  }
+  double fref = freqs_mhz[0];
+  for (int c = 1; c < nchans; ++c) fref = std::max(fref, freqs_mhz[c]);
+  double* d_freqs = nullptr;
+  int32_t* d_err = nullptr;
+  DD_TRY(dalloc(&p->d_shifts, sizeof(int32_t) * (size_t)total_rows * p->C4, "delay table"));
+  DD_TRY(dalloc(&d_freqs, sizeof(double) * nchans, "frequencies"));
+  if (dalloc(&d_err, sizeof(int32_t), "flag")) {
+    cudaFree(d_freqs);
+    free_plan(p);
+    return DD_ERR_NOMEM;
+  }
+  {
+    cudaError_t e = cudaMemcpy(d_freqs, freqs_mhz, sizeof(double) * nchans, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(int32_t));
+    if (e == cudaSuccess)
+      e = ddk::launch_shift_table(d_freqs, nchans, p->C4, fref, tsamp_s, sr.data(), nranges,
+                                  (int32_t)total_rows, p->d_shifts, d_err, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int32_t herr = 0;
+    std::vector<int32_t> full((size_t)total_rows * p->C4);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof herr, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(full.data(), p->d_shifts, sizeof(int32_t) * full.size(),
+                     cudaMemcpyDeviceToHost);
+    cudaFree(d_freqs);
+    cudaFree(d_err);
+    if (e != cudaSuccess) {
+      free_plan(p);
+      return fail(DD_ERR_CUDA, "delay table: %s", cudaGetErrorString(e));
+    }
+    p->launches += 1;
+    if (herr) {
+      free_plan(p);
+      return fail(DD_ERR_ARG, "a delay does not fit a non-negative int32 sample count");
+    }
+    p->h_shifts.resize((size_t)total_rows * nchans);
+    for (int64_t rr = 0; rr < total_rows; ++rr)
+      std::memcpy(&p->h_shifts[rr * nchans], &full[rr * p->C4], sizeof(int32_t) * nchans);
+    // overlap O = d_max * ceil(max_r(d_r * max s_r) / d_max)
+    int64_t need = 0;
+    for (int r = 0; r < nranges; ++r) {
+      int64_t smax = 0;
+      for (int64_t rr = p->row0[r]; rr < p->row0[r] + ranges[r].n_trials; ++rr)
+        for (int c = 0; c < nchans; ++c) smax = std::max<int64_t>(smax, p->h_shifts[rr * nchans + c]);
+      need = std::max<int64_t>(need, smax * ranges[r].decimation);
+    }
+    p->O = round_up(need, dmax);
+  }
+  // history kept on the device: O rounded up so every ring row starts 256-byte aligned
+  p->H = round_up(p->O, 256);
+  const int64_t span = p->H + p->L;
+  p->R1 = round_up(span, 256) + 256;
+  for (int l = 1; l <= p->levels; ++l) p->Rd[l] = round_up(span >> l, 128) + 128;
+  p->series_off.resize(nranges);
+  p->series_stride.resize(nranges);
+  int64_t off = 0;
+  for (int r = 0; r < nranges; ++r) {
+    const int64_t st = round_up(p->L / ranges[r].decimation, 32);
+    p->series_off[r] = off;
+    p->series_stride[r] = st;
+    off += st * ranges[r].n_trials;
+  }
+  p->series_elems = off;
+
+  // ---- buffers (all allocation happens here)
+  DD_TRY(dalloc(&p->hist, (size_t)p->C4 * std::max<int64_t>(p->H, 1), "history"));
+  DD_TRYCK(cudaMemset(p->hist, 0, (size_t)p->C4 * std::max<int64_t>(p->H, 1)));
+  DD_TRYCK(cudaEventCreateWithFlags(&p->ev_hist, cudaEventDisableTiming));
+  DD_TRYCK(cudaStreamCreateWithFlags(&p->io, cudaStreamNonBlocking));
+  DD_TRYCK(cudaEventCreateWithFlags(&p->ev_io, cudaEventDisableTiming));
+  if (cudaMallocHost((void**)&p->h_cands, sizeof(dd_cand_t) * p->opts.max_cands) != cudaSuccess) {
+    cudaGetLastError();
+    p->h_cands = nullptr;
+    free_plan(p);
+    return fail(DD_ERR_NOMEM, "pinned candidate buffer");
+  }
+  p->slots.resize(o.n_streams);
+  for (auto& s : p->slots) {
+    DD_TRYCK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+    DD_TRYCK(cudaEventCreateWithFlags(&s.ev_free, cudaEventDisableTiming));
+    DD_TRYCK(cudaEventCreateWithFlags(&s.ev_sps, cudaEventDisableTiming));
+    DD_TRY(dalloc(&s.staging, (size_t)p->L * nchans, "staging"));
+    DD_TRY(dalloc(&s.ring1, (size_t)p->C4 * p->R1, "ring"));
+    DD_TRYCK(cudaMemset(s.ring1, 0, (size_t)p->C4 * p->R1));
+    for (int l = 1; l <= p->levels; ++l) {
+      DD_TRY(dalloc(&s.ringd[l], sizeof(uint16_t) * (size_t)p->C4 * p->Rd[l], "decimated ring"));
+      DD_TRYCK(cudaMemset(s.ringd[l], 0, sizeof(uint16_t) * (size_t)p->C4 * p->Rd[l]));
+    }
+    DD_TRY(dalloc(&s.series, sizeof(int32_t) * (size_t)p->series_elems, "series"));
+    DD_TRY(dalloc(&s.mom, sizeof(ddk::Moments) * (size_t)total_rows, "moments"));
+    DD_TRY(dalloc(&s.cands, sizeof(dd_cand_t) * (size_t)p->opts.max_cands, "candidates"));
+    DD_TRY(dalloc(&s.d_count, sizeof(unsigned long long), "count"));
+    if (cudaMallocHost((void**)&s.h_count, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      s.h_count = nullptr;
+      free_plan(p);
+      return fail(DD_ERR_NOMEM, "pinned count");
+    }
+  }
+  if (o.flags & DD_FLAG_TIMING) {
+    p->tev.resize(2 * 1024);
+    for (auto& e : p->tev) DD_TRYCK(cudaEventCreate(&e));
+  }
+  DD_TRYCK(cudaDeviceSynchronize());
+#undef DD_TRY
+#undef DD_TRYCK
+  *out = p;
+  return DD_OK;
+}
+
+int dd_plan_info(dd_plan_t p, int64_t* overlap, int32_t* ntrials, const int32_t** shifts) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (overlap) *overlap = p->O;
+  if (ntrials) *ntrials = p->total_rows;
+  if (shifts) *shifts = p->h_shifts.data();
+  return DD_OK;
+}
+
+int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (!chunk) return fail(DD_ERR_ARG, "chunk is NULL");
+  if (nsamp <= 0 || nsamp > p->L || nsamp % p->dmax != 0)
+    return fail(DD_ERR_ARG, "nsamp %lld must be in 1..chunk_len and a multiple of %d",
+                (long long)nsamp, p->dmax);
+  DD_CK(cudaSetDevice(p->device));
+  const int64_t seq = p->next_seq;
+  Slot& s = p->slots[seq % p->slots.size()];
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : s.stream;
+  // the slot's previous chunk (possibly on another stream) must be finished with its buffers
+  if (s.seq >= 0) DD_CK(cudaStreamWaitEvent(st, s.ev_free, 0));
+  if (seq > 0) DD_CK(cudaStreamWaitEvent(st, p->ev_hist, 0));
+
+  cudaPointerAttributes attr;
+  DD_CK(cudaPointerGetAttributes(&attr, chunk));
+  const uint8_t* src = chunk;
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+    DD_CK(cudaMemcpyAsync(s.staging, chunk, (size_t)nsamp * p->C, cudaMemcpyHostToDevice, st));
+    src = s.staging;
+  }
+  const int64_t H = p->H;
+  if (seq > 0 && H > 0)
+    DD_CK(cudaMemcpy2DAsync(s.ring1, p->R1, p->hist, H, H, p->C4, cudaMemcpyDeviceToDevice, st));
+  DD_CK(ddk::launch_corner_turn(src, nsamp, p->C, s.ring1, p->R1, H, st));
+  p->launches += 1;
+  if (H > 0) {
+    DD_CK(cudaMemcpy2DAsync(p->hist, H, s.ring1 + nsamp, p->R1, H, p->C4,
+                            cudaMemcpyDeviceToDevice, st));
+    DD_CK(cudaEventRecord(p->ev_hist, st));
+  }
+  // hierarchical x2 decimation of the whole ring (history + new samples)
+  for (int l = 1; l <= p->levels; ++l) {
+    const void* in = (l == 1) ? (const void*)s.ring1 : (const void*)s.ringd[l - 1];
+    const int64_t in_stride = (l == 1) ? p->R1 : p->Rd[l - 1];
+    DD_CK(ddk::launch_decimate(in, l > 1, in_stride, s.ringd[l], p->Rd[l], p->C4,
+                               (H + nsamp) >> l, st));
+    p->launches += 1;
+  }
+  const int64_t T = p->T_total;
+  const int64_t lo = std::max<int64_t>(0, T - p->O), hi = std::max<int64_t>(0, T + nsamp - p->O);
+  for (size_t r = 0; r < p->ranges.size(); ++r) {
+    const int d = p->ranges[r].decimation;
+    const int l = ilog2(d);
+    ddk::DedispRange R;
+    R.xd = (l == 0) ? (const void*)s.ring1 : (const void*)s.ringd[l];
+    R.xd_stride = (l == 0) ? p->R1 : p->Rd[l];
+    R.m0 = (lo - (T - H)) / d;
+    R.nout = (hi - lo) / d;
+    R.y = s.series + p->series_off[r];
+    R.y_stride = p->series_stride[r];
+    R.mom = s.mom + p->row0[r];
+    R.shifts = p->d_shifts + (int64_t)p->row0[r] * p->C4;
+    R.n_trials = p->ranges[r].n_trials;
+    R.is_u16 = l > 0;
+    if (R.nout <= 0) continue;
+    int64_t ts;
+    int rc = timing_begin(p, st, &ts);
+    if (rc) return rc;
+    DD_CK(ddk::launch_dedisp_naive(R, p->C4, st));
+    rc = timing_end(p, st, ts);
+    if (rc) return rc;
+    DD_CK(ddk::launch_moments(R.y, R.n_trials, R.nout, R.y_stride, R.mom, st));
+    p->launches += 2;
+  }
+  DD_CK(cudaEventRecord(s.ev_free, st));
+  s.used = st;
+  s.seq = seq;
+  s.T = T;
+  s.n = nsamp;
+  s.lo = lo;
+  s.hi = hi;
+  s.searched = false;
+  p->T_total += nsamp;
+  p->next_seq += 1;
+  return DD_OK;
+}
+
+int dd_series(dd_plan_t p, int32_t range, const int32_t** dev_ptr, int64_t* len, int64_t* stride,
+              int64_t* j0) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (range < 0 || range >= (int32_t)p->ranges.size()) return fail(DD_ERR_ARG, "bad range");
+  if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
+  const Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
+  const int d = p->ranges[range].decimation;
+  if (dev_ptr) *dev_ptr = s.series + p->series_off[range];
+  if (len) *len = (s.hi - s.lo) / d;
+  if (stride) *stride = p->series_stride[range];
+  if (j0) *j0 = s.lo / d;
+  return DD_OK;
+}
+
+int sps_run(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (!widths || nwidths < 1 || nwidths > ddk::kMaxWidths)
+    return fail(DD_ERR_ARG, "nwidths must be 1..%d", ddk::kMaxWidths);
+  for (int k = 0; k < nwidths; ++k) {
+    if (widths[k] < 1 || widths[k] > p->opts.max_width)
+      return fail(DD_ERR_ARG, "width %d outside 1..max_width", widths[k]);
+    if (k > 0 && widths[k] <= widths[k - 1])
+      return fail(DD_ERR_ARG, "widths must be strictly increasing");
+  }
+  if (!std::isfinite(threshold)) return fail(DD_ERR_ARG, "threshold must be finite");
+  if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
+  Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
+  if (s.searched) return fail(DD_ERR_STATE, "the latest chunk was already searched");
+  DD_CK(cudaSetDevice(p->device));
+  cudaStream_t st = s.used;
+  DD_CK(cudaMemsetAsync(s.d_count, 0, sizeof(unsigned long long), st));
+  for (size_t r = 0; r < p->ranges.size(); ++r) {
+    const int d = p->ranges[r].decimation;
+    ddk::SpsArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.nw = 0;
+    for (int k = 0; k < nwidths; ++k)
+      if (widths[k] >= d && widths[k] % d == 0) a.wd[a.nw++] = widths[k] / d;
+    a.n = (s.hi - s.lo) / d;
+    if (a.nw == 0 || a.n <= 0) continue;
+    a.y = s.series + p->series_off[r];
+    a.stride = p->series_stride[r];
+    a.mom = s.mom + p->row0[r];
+    a.n_trials = p->ranges[r].n_trials;
+    a.range = (int32_t)r;
+    a.d = d;
+    a.block = p->opts.peak_block;
+    a.J0 = s.lo / d;
+    a.hist = (int32_t)round_up(std::max(a.wd[a.nw - 1] - 1, 0), 256);
+    a.threshold = threshold;
+    a.cands = s.cands;
+    a.count = s.d_count;
+    a.cap = p->opts.max_cands;
+    DD_CK(ddk::launch_sps(a, st));
+    p->launches += 1;
+  }
+  DD_CK(cudaMemcpyAsync(s.h_count, s.d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        st));
+  DD_CK(cudaEventRecord(s.ev_sps, st));
+  DD_CK(cudaEventRecord(s.ev_free, st));
+  s.searched = true;
+  return DD_OK;
+}
+
+int dd_candidates(dd_plan_t p, int64_t seq, dd_cand_t* out, int64_t cap, int64_t* ncands,
+                  int64_t timeout_ms) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (!ncands || (cap > 0 && !out) || cap < 0) return fail(DD_ERR_ARG, "bad output arguments");
+  const int64_t S = (int64_t)p->slots.size();
+  if (seq < 0 || seq >= p->next_seq || seq < p->next_seq - S)
+    return fail(DD_ERR_STATE, "chunk %lld is not among the last %lld chunks", (long long)seq,
+                (long long)S);
+  Slot& s = p->slots[seq % S];
+  if (s.seq != seq || !s.searched) return fail(DD_ERR_STATE, "chunk %lld was not searched",
+                                               (long long)seq);
+  DD_CK(cudaSetDevice(p->device));
+  int rc = wait_event(s.ev_sps, timeout_ms);
+  if (rc) return rc;
+  const int64_t count = (int64_t)*s.h_count;
+  const int64_t kept = std::min<int64_t>(count, p->opts.max_cands);
+  if (kept > 0) {
+    DD_CK(cudaStreamWaitEvent(p->io, s.ev_sps, 0));
+    DD_CK(cudaMemcpyAsync(p->h_cands, s.cands, sizeof(dd_cand_t) * kept, cudaMemcpyDeviceToHost,
+                          p->io));
+    DD_CK(cudaEventRecord(p->ev_io, p->io));
+    rc = wait_event(p->ev_io, timeout_ms);
+    if (rc) return rc;
+    std::sort(p->h_cands, p->h_cands + kept, [](const dd_cand_t& a, const dd_cand_t& b) {
+      if (a.range != b.range) return a.range < b.range;
+      if (a.trial != b.trial) return a.trial < b.trial;
+      if (a.t_start != b.t_start) return a.t_start < b.t_start;
+      return a.width < b.width;
+    });
+    std::memcpy(out, p->h_cands, sizeof(dd_cand_t) * std::min(kept, cap));
+  }
+  *ncands = count;
+  if (count > cap || count > p->opts.max_cands)
+    return fail(DD_ERR_CAP, "%lld candidates exceed the buffer (cap %lld, max_cands %lld)",
+                (long long)count, (long long)cap, (long long)p->opts.max_cands);
+  return DD_OK;
+}
+
+int dd_sync(dd_plan_t p) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  DD_CK(cudaSetDevice(p->device));
+  for (auto& s : p->slots) {
+    DD_CK(cudaStreamSynchronize(s.stream));
+    if (s.used && s.used != s.stream) DD_CK(cudaStreamSynchronize(s.used));
+  }
+  DD_CK(cudaStreamSynchronize(p->io));
+  return DD_OK;
+}
+
+int dd_stats(dd_plan_t p, int64_t* launches, double* dedisp_ms, int64_t* dedisp_launches,
+             int32_t reset) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  DD_CK(cudaSetDevice(p->device));
+  int rc = harvest_timing(p, true);
+  if (rc) return rc;
+  if (launches) *launches = p->launches;
+  if (dedisp_ms) *dedisp_ms = p->dedisp_ms;
+  if (dedisp_launches) *dedisp_launches = p->dedisp_launches;
+  if (reset) {
+    p->launches = 0;
+    p->dedisp_ms = 0;
+    p->dedisp_launches = 0;
+  }
+  return DD_OK;
+}
+
+void dd_plan_destroy(dd_plan_t p) { free_plan(p); }
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dd.h"
+
+namespace ddk {
+
+constexpr int kMaxRanges = 64;
+constexpr int kMaxWidths = 16;
+
+// Exact moments of one (range, trial) series over a chunk window: S1 = sum y, S2 = sum y^2 as a
+// 128-bit value (s2lo, s2hi). 32 bytes so one trial's record is one sector.
+struct Moments {
+  unsigned long long s1, s2lo, s2hi, pad;
+};
+
+// Per-range parameters of the delay-table kernel.
+struct ShiftRange {
+  double dm_start, dm_step;
+  int32_t n_trials, decimation, row0, pad;
+};
+
+// One launch of the search kernel handles one range of one chunk.
+struct SpsArgs {
+  const int32_t* y;        // [n_trials][stride]
+  int64_t stride;
+  int64_t n;               // window length
+  const Moments* mom;      // [n_trials]
+  int32_t n_trials;
+  int32_t range;
+  int32_t d;
+  int32_t block;           // samples per candidate block (power of two <= 256)
+  int64_t J0;              // global decimated index of window sample 0
+  int32_t nw;
+  int32_t hist;            // largest decimated width - 1 rounded up to 32
+  int32_t wd[kMaxWidths];  // decimated widths, increasing
+  float threshold;
+  int32_t pad;
+  dd_cand_t* cands;
+  unsigned long long* count;
+  int64_t cap;
+};
+
+// Work list entry of the tiled dedispersion kernel (one CTA).
+struct DedispTile {
+  int32_t range;        // range index
+  int32_t trial0;       // first trial of the tile within the range
+  int32_t ntr;          // trials in the tile (<= kTileTrials)
+  int32_t j0;           // first window sample of the tile
+};
+
+// Per-range geometry of one chunk for the tiled dedispersion kernel.
+struct DedispRange {
+  const void* xd;          // decimated ring: uint8 (d == 1) or uint16 [C4][xd_stride]
+  int64_t xd_stride;       // elements
+  int64_t m0;              // ring column of window sample 0
+  int64_t nout;            // window length
+  int32_t* y;              // [n_trials][y_stride]
+  int64_t y_stride;
+  Moments* mom;            // [n_trials]
+  const int32_t* shifts;   // [n_trials][C4]
+  int32_t n_trials;
+  int32_t is_u16;
+};
+
+// ---- launchers (dd_kernels.cu); each returns the cudaGetLastError() of its launch
+cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t c4, double fref,
+                               double tsamp, const ShiftRange* ranges, int32_t nranges,
+                               int32_t total_rows, int32_t* shifts, int32_t* err,
+                               cudaStream_t st);
+cudaError_t launch_corner_turn(const uint8_t* in, int64_t n, int32_t nchans, uint8_t* ring,
+                               int64_t ring_stride, int64_t col0, cudaStream_t st);
+cudaError_t launch_decimate(const void* in, int in_is_u16, int64_t in_stride, uint16_t* out,
+                            int64_t out_stride, int32_t c4, int64_t n_out, cudaStream_t st);
+cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t c4, cudaStream_t st);
+cudaError_t launch_moments(const int32_t* y, int32_t ntr, int64_t n, int64_t stride, Moments* mom,
+                           cudaStream_t st);
+cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st);
+
+}  // namespace ddk

@@ -1,0 +1,444 @@
+// Kernels of the dedispersion + single-pulse-search path (sm_103a), except the tiled
+// dedispersion kernel (dd_dedisp.cu).
+//
+//   k_shift_table : FP64 delay table, one IEEE operation at a time (Sec. 3 DM plan)
+//   k_corner_turn : time-major uint8 spectra -> channel-major ring (Sec. 1 time chunks)
+//   k_decimate    : exact x2 time decimation, uint8/uint16 -> uint16
+//   k_dedisp_naive: one thread per output sample (reference-shaped; testing aid)
+//   k_moments     : exact S1 / 128-bit S2 of each series window (Sec. 2.2)
+//   k_sps         : boxcar SNR over prefix sums + block peak finding (Sec. 2.2)
+#include <math.h>
+
+#include "dd_internal.h"
+
+namespace ddk {
+
+// ------------------------------------------------------------------ delay table
+
+__constant__ ShiftRange c_ranges[kMaxRanges];
+
+__global__ void k_shift_table(const double* __restrict__ freqs, int32_t nchans, int32_t c4,
+                              double fref, double tsamp, int32_t nranges, int32_t total_rows,
+                              int32_t* __restrict__ shifts, int32_t* __restrict__ err) {
+  const int64_t total = (int64_t)total_rows * c4;
+  // k_DM = 4.148808e3 s MHz^2 pc^-1 cm^3 (textbook cold-plasma constant).
+  const double kdm = 4.148808e3;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t row = (int32_t)(e / c4);
+    const int32_t c = (int32_t)(e - (int64_t)row * c4);
+    int r = 0;
+    while (r + 1 < nranges && row >= c_ranges[r + 1].row0) ++r;
+    const ShiftRange R = c_ranges[r];
+    int32_t s = 0;
+    if (c < nchans) {
+      // dm = start + i*step; a = 1/(f*f); b = 1/(fref*fref); tau = (k*dm)*(a-b);
+      // x = tau/(tsamp*d) + 0.5; s = floor(x).  Explicit round-to-nearest intrinsics: no FMA.
+      const double dm = __dadd_rn(R.dm_start, __dmul_rn((double)(row - R.row0), R.dm_step));
+      const double f = freqs[c];
+      const double a = __ddiv_rn(1.0, __dmul_rn(f, f));
+      const double b = __ddiv_rn(1.0, __dmul_rn(fref, fref));
+      const double tau = __dmul_rn(__dmul_rn(kdm, dm), __dsub_rn(a, b));
+      const double x = __dadd_rn(__ddiv_rn(tau, __dmul_rn(tsamp, (double)R.decimation)), 0.5);
+      const double fl = floor(x);
+      if (!(fl >= 0.0 && fl <= 2147483647.0)) {
+        atomicOr(err, 1);
+        s = 0;
+      } else {
+        s = (int32_t)fl;
+      }
+    }
+    shifts[e] = s;
+  }
+}
+
+cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t c4, double fref,
+                               double tsamp, const ShiftRange* ranges, int32_t nranges,
+                               int32_t total_rows, int32_t* shifts, int32_t* err,
+                               cudaStream_t st) {
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_ranges, ranges, sizeof(ShiftRange) * nranges, 0,
+                                          cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)total_rows * c4;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  k_shift_table<<<(unsigned)blocks, 256, 0, st>>>(freqs, nchans, c4, fref, tsamp, nranges,
+                                                  total_rows, shifts, err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ corner turn
+
+// 64 samples x 64 channels per CTA. 16-byte loads of spectra into shared memory, a 4x4 byte
+// transpose in registers (PRMT), 4-byte stores of channel rows.
+__global__ void __launch_bounds__(256) k_corner_turn16(const uint8_t* __restrict__ in, int64_t n,
+                                                       int32_t nchans, uint8_t* __restrict__ ring,
+                                                       int64_t stride, int64_t col0) {
+  __shared__ uint32_t S[64][17];
+  const int tid = threadIdx.x;
+  const int64_t t0 = (int64_t)blockIdx.x * 64;
+  const int32_t c0 = blockIdx.y * 64;
+  {
+    const int r = tid >> 2, q = tid & 3;
+    const int64_t t = t0 + r;
+    const int32_t c = c0 + 16 * q;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (t < n && c < nchans) v = __ldg(reinterpret_cast<const uint4*>(in + t * nchans + c));
+    S[r][4 * q + 0] = v.x;
+    S[r][4 * q + 1] = v.y;
+    S[r][4 * q + 2] = v.z;
+    S[r][4 * q + 3] = v.w;
+  }
+  __syncthreads();
+  const int tb = tid & 15, cw = tid >> 4;
+  const uint32_t w0 = S[4 * tb + 0][cw], w1 = S[4 * tb + 1][cw];
+  const uint32_t w2 = S[4 * tb + 2][cw], w3 = S[4 * tb + 3][cw];
+  const uint32_t a0 = __byte_perm(w0, w1, 0x5140), a1 = __byte_perm(w0, w1, 0x7362);
+  const uint32_t a2 = __byte_perm(w2, w3, 0x5140), a3 = __byte_perm(w2, w3, 0x7362);
+  uint32_t o[4];
+  o[0] = __byte_perm(a0, a2, 0x5410);
+  o[1] = __byte_perm(a0, a2, 0x7632);
+  o[2] = __byte_perm(a1, a3, 0x5410);
+  o[3] = __byte_perm(a1, a3, 0x7632);
+  const int64_t t = t0 + 4 * tb;
+  if (t >= n) return;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int32_t c = c0 + 4 * cw + j;
+    if (c < nchans)
+      *reinterpret_cast<uint32_t*>(ring + (int64_t)c * stride + col0 + t) = o[j];
+  }
+}
+
+// Any channel count / alignment: one byte per thread.
+__global__ void k_corner_turn1(const uint8_t* __restrict__ in, int64_t n, int32_t nchans,
+                               uint8_t* __restrict__ ring, int64_t stride, int64_t col0) {
+  const int64_t total = n * nchans;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / nchans;
+    const int32_t c = (int32_t)(e - t * nchans);
+    ring[(int64_t)c * stride + col0 + t] = in[e];
+  }
+}
+
+cudaError_t launch_corner_turn(const uint8_t* in, int64_t n, int32_t nchans, uint8_t* ring,
+                               int64_t ring_stride, int64_t col0, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const bool fast = (nchans % 16 == 0) && (((uintptr_t)in & 15) == 0) && (ring_stride % 4 == 0) &&
+                    (col0 % 4 == 0) && (((uintptr_t)ring & 3) == 0);
+  if (fast) {
+    dim3 grid((unsigned)((n + 63) / 64), (unsigned)((nchans + 63) / 64));
+    k_corner_turn16<<<grid, 256, 0, st>>>(in, n, nchans, ring, ring_stride, col0);
+  } else {
+    int64_t blocks = (n * nchans + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_corner_turn1<<<(unsigned)blocks, 256, 0, st>>>(in, n, nchans, ring, ring_stride, col0);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ decimation
+
+// out[c][m] = in[c][2m] + in[c][2m+1], four outputs per thread.
+__global__ void k_decimate_u8(const uint8_t* __restrict__ in, int64_t in_stride,
+                              uint16_t* __restrict__ out, int64_t out_stride, int64_t n_out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (4 * k >= n_out) return;
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(in + c * in_stride + 8 * k));
+  const uint32_t lo = (v.x & 0xFFu) + ((v.x >> 8) & 0xFFu);
+  const uint32_t hi = ((v.x >> 16) & 0xFFu) + (v.x >> 24);
+  const uint32_t lo2 = (v.y & 0xFFu) + ((v.y >> 8) & 0xFFu);
+  const uint32_t hi2 = ((v.y >> 16) & 0xFFu) + (v.y >> 24);
+  uint2 o;
+  o.x = lo | (hi << 16);
+  o.y = lo2 | (hi2 << 16);
+  *reinterpret_cast<uint2*>(out + c * out_stride + 4 * k) = o;
+}
+
+__global__ void k_decimate_u16(const uint16_t* __restrict__ in, int64_t in_stride,
+                               uint16_t* __restrict__ out, int64_t out_stride, int64_t n_out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (4 * k >= n_out) return;
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + c * in_stride + 8 * k));
+  const uint32_t s0 = (v.x & 0xFFFFu) + (v.x >> 16), s1 = (v.y & 0xFFFFu) + (v.y >> 16);
+  const uint32_t s2 = (v.z & 0xFFFFu) + (v.z >> 16), s3 = (v.w & 0xFFFFu) + (v.w >> 16);
+  uint2 o;
+  o.x = s0 | (s1 << 16);
+  o.y = s2 | (s3 << 16);
+  *reinterpret_cast<uint2*>(out + c * out_stride + 4 * k) = o;
+}
+
+cudaError_t launch_decimate(const void* in, int in_is_u16, int64_t in_stride, uint16_t* out,
+                            int64_t out_stride, int32_t c4, int64_t n_out, cudaStream_t st) {
+  if (n_out <= 0) return cudaSuccess;
+  dim3 grid((unsigned)(((n_out + 3) / 4 + 255) / 256), (unsigned)c4);
+  if (in_is_u16)
+    k_decimate_u16<<<grid, 256, 0, st>>>(static_cast<const uint16_t*>(in), in_stride, out,
+                                         out_stride, n_out);
+  else
+    k_decimate_u8<<<grid, 256, 0, st>>>(static_cast<const uint8_t*>(in), in_stride, out,
+                                        out_stride, n_out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ naive dedispersion
+
+template <typename T>
+__global__ void k_dedisp_naive(const T* __restrict__ xd, int64_t stride, int32_t c4, int64_t m0,
+                               int64_t nout, const int32_t* __restrict__ shifts,
+                               int32_t* __restrict__ y, int64_t y_stride) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t i = blockIdx.y;
+  if (j >= nout) return;
+  const int32_t* s = shifts + (int64_t)i * c4;
+  int32_t acc = 0;
+  for (int32_t c = 0; c < c4; ++c) acc += (int32_t)xd[(int64_t)c * stride + m0 + j + s[c]];
+  y[(int64_t)i * y_stride + j] = acc;
+}
+
+cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t c4, cudaStream_t st) {
+  if (r.nout <= 0 || r.n_trials <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((r.nout + 255) / 256), (unsigned)r.n_trials);
+  if (r.is_u16)
+    k_dedisp_naive<uint16_t><<<grid, 256, 0, st>>>(static_cast<const uint16_t*>(r.xd), r.xd_stride,
+                                                   c4, r.m0, r.nout, r.shifts, r.y, r.y_stride);
+  else
+    k_dedisp_naive<uint8_t><<<grid, 256, 0, st>>>(static_cast<const uint8_t*>(r.xd), r.xd_stride,
+                                                  c4, r.m0, r.nout, r.shifts, r.y, r.y_stride);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ moments
+
+struct U128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ U128 add128(U128 a, U128 b) {
+  U128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_moments(const int32_t* __restrict__ y, int64_t n,
+                                                 int64_t stride, Moments* __restrict__ mom) {
+  const int32_t i = blockIdx.x;
+  const int32_t* yi = y + (int64_t)i * stride;
+  unsigned long long s1 = 0;
+  U128 s2 = {0, 0};
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const int64_t v = yi[j];
+    s1 += (unsigned long long)v;
+    s2 = add128(s2, U128{(unsigned long long)(v * v), 0});
+  }
+  __shared__ unsigned long long sh[3][8];
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    U128 o;
+    o.lo = __shfl_xor_sync(0xffffffffu, s2.lo, off);
+    o.hi = __shfl_xor_sync(0xffffffffu, s2.hi, off);
+    s2 = add128(s2, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh[0][w] = s1;
+    sh[1][w] = s2.lo;
+    sh[2][w] = s2.hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0;
+    U128 b = {0, 0};
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += sh[0][k];
+      b = add128(b, U128{sh[1][k], sh[2][k]});
+    }
+    mom[i].s1 = a;
+    mom[i].s2lo = b.lo;
+    mom[i].s2hi = b.hi;
+    mom[i].pad = 0;
+  }
+}
+
+cudaError_t launch_moments(const int32_t* y, int32_t ntr, int64_t n, int64_t stride, Moments* mom,
+                           cudaStream_t st) {
+  if (ntr <= 0) return cudaSuccess;
+  k_moments<<<ntr, 256, 0, st>>>(y, n, stride, mom);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ single pulse search
+
+// Correctly rounded unsigned 128-bit -> double: the top 64 significant bits with a sticky bit
+// for everything below, converted with round-to-nearest-even, then scaled by a power of two.
+__device__ __forceinline__ double u128_to_f64(unsigned long long hi, unsigned long long lo) {
+  if (hi == 0) return __ull2double_rn(lo);
+  const int lz = __clzll((long long)hi);
+  const int sh = 64 - lz;  // 1..64
+  unsigned long long top, sticky;
+  if (sh == 64) {
+    top = hi;
+    sticky = lo != 0;
+  } else {
+    top = (hi << lz) | (lo >> sh);
+    sticky = (lo << lz) != 0;
+  }
+  return ldexp(__ull2double_rn(top | sticky), sh);
+}
+
+constexpr int kSpsThreads = 256;
+constexpr int kSpsSeg = 1024;  // window samples per pass
+
+__global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
+  extern __shared__ long long P[];  // [1 + hist + kSpsSeg]: P[0] = 0, P[1+u] = sum_{k<=u}
+  __shared__ double den[kMaxWidths];
+  __shared__ float inv32[kMaxWidths];
+  __shared__ long long warp_tot[kSpsThreads / 32];
+
+  const int32_t i = blockIdx.x;
+  const int tid = threadIdx.x;
+  const Moments m = a.mom[i];
+  const long long n = a.n;
+  if (n <= 0) return;
+  const long long s1 = (long long)m.s1;
+  // V = n*S2 - S1^2 in 128 bits (exact; S1 >= 0 because every series value is a sum of
+  // non-negative samples)
+  const unsigned long long un = (unsigned long long)n, us1 = (unsigned long long)s1;
+  const unsigned long long p_lo = un * m.s2lo;
+  const unsigned long long p_hi = __umul64hi(un, m.s2lo) + un * m.s2hi;
+  const unsigned long long q_lo = us1 * us1, q_hi = __umul64hi(us1, us1);
+  const unsigned long long v_lo = p_lo - q_lo;
+  const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
+  if (v_lo == 0 && v_hi == 0) return;  // constant series: no candidates
+  const double sq = sqrt(u128_to_f64(v_hi, v_lo));
+  if (tid < a.nw) {
+    den[tid] = sqrt((double)a.wd[tid]) * sq;
+    inv32[tid] = (float)(1.0 / den[tid]);
+  }
+  const int H = a.hist;
+  const int span = H + kSpsSeg;
+  const int E = span / kSpsThreads;  // entries per thread in the scan (span % 256 == 0)
+  const int32_t* yi = a.y + (int64_t)i * a.stride;
+  const int B = a.block;
+  const float thr = a.threshold;
+  const float margin = 1e-3f * fmaxf(1.0f, fabsf(thr));
+  if (tid == 0) P[0] = 0;
+
+  for (long long seg0 = 0; seg0 < n; seg0 += kSpsSeg) {
+    // ---- prefix sums of y[seg0-H .. seg0+kSpsSeg), zero outside the window
+    long long run = 0;
+    long long vals[8];
+    const long long base = seg0 - H + (long long)tid * E;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (e < E) {
+        const long long k = base + e;
+        run += (k >= 0 && k < n) ? (long long)yi[k] : 0ll;
+        vals[e] = run;
+      }
+    }
+    // exclusive scan of per-thread totals
+    long long incl = run;
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int off = 1; off < 32; off <<= 1) {
+      const long long o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    __syncthreads();  // previous pass finished reading P / warp_tot
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    long long woff = 0;
+    for (int k = 0; k < wid; ++k) woff += warp_tot[k];
+    const long long excl = woff + incl - run;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (e < E) P[1 + tid * E + e] = excl + vals[e];
+    __syncthreads();
+
+    // ---- boxcars, block maxima, candidates
+    for (int e = 0; e < kSpsSeg / kSpsThreads; ++e) {
+      const long long j = seg0 + e * kSpsThreads + tid;  // window sample
+      const int u = H + e * kSpsThreads + tid;           // its entry in P (before the +1)
+      const bool leader = (tid & (B - 1)) == 0;
+      int32_t bestB[kMaxWidths];
+      int32_t bestJ[kMaxWidths];
+      float best32 = -INFINITY;
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < kMaxWidths; ++k) {
+        if (k < a.nw) {
+          const int w = a.wd[k];
+          const bool valid = (j < n) && (j >= w - 1);
+          unsigned long long key = 0;
+          if (valid) {
+            const long long bw = P[1 + u] - P[1 + u - w];
+            key = ((unsigned long long)bw << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)(tid & (B - 1)));
+          }
+          for (int off = B >> 1; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
+            key = o > key ? o : key;
+          }
+          bestB[k] = -1;
+          bestJ[k] = 0;
+          if (key != 0) {
+            bestB[k] = (int32_t)(key >> 32);
+            bestJ[k] = (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
+            const long long num = n * (long long)bestB[k] - (long long)w * s1;
+            best32 = fmaxf(best32, (float)num * inv32[k]);
+            any = true;
+          }
+        }
+      }
+      if (leader && any && best32 >= thr - margin) {
+        // exact decision in FP64, in the oracle's evaluation order
+        double bs = 0.0;
+        long long bj = 0;
+        int bw = 0;
+        bool have = false;
+        const long long jb = j;  // block start (leader has offset 0 in its block)
+#pragma unroll
+        for (int k = 0; k < kMaxWidths; ++k) {
+          if (k < a.nw && bestB[k] >= 0) {
+            const int w = a.wd[k];
+            const long long num = n * (long long)bestB[k] - (long long)w * s1;
+            const double snr = (double)num / den[k];
+            const long long jk = jb + bestJ[k];
+            if (!have || snr > bs || (snr == bs && jk < bj)) {
+              have = true;
+              bs = snr;
+              bj = jk;
+              bw = w;
+            }
+          }
+        }
+        if (have && bs >= (double)thr) {
+          const unsigned long long idx = atomicAdd(a.count, 1ull);
+          if ((long long)idx < a.cap) {
+            dd_cand_t c;
+            c.trial = i;
+            c.range = a.range;
+            c.t_start = (a.J0 + bj - bw + 1) * (long long)a.d;
+            c.width = bw * a.d;
+            c.pad = 0;
+            c.snr = bs;
+            a.cands[idx] = c;
+          }
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st) {
+  if (a.n <= 0 || a.n_trials <= 0 || a.nw <= 0) return cudaSuccess;
+  const size_t smem = sizeof(long long) * (size_t)(1 + a.hist + kSpsSeg);
+  k_sps<<<a.n_trials, kSpsThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ddk

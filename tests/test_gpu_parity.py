@@ -1,0 +1,273 @@
+"""GPU path (through the C ABI) against the CPU oracle.
+
+Dedispersed series and moments bit-exact; candidates per block with SNR within
+1e-5 relative (tests/_parity.py). Covers the tiny workload whole and chunked
+over 1 and 4 streams, multi-range decimated plans with ragged chunks and
+ragged channel counts, every input kind (device, pinned, pageable), pipelined
+streams, an empty first window, and the full-size 4096-channel workload on
+sampled trials in the benchmark's launch configuration.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import configs
+from _parity import compare_candidates
+
+torch = pytest.importorskip("torch")
+import paper_2101_00941_gb300 as dd  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    dd.build()
+    dd.lib()
+
+
+def _arrivals(w):
+    f = w.freqs()
+    return lambda dm: oracle.delay_samples(f, w.tsamp, dm)
+
+
+def _as_input(part, kind):
+    if kind == "device":
+        return torch.from_numpy(part).cuda()
+    if kind == "pinned":
+        return torch.from_numpy(part).pin_memory()
+    return np.ascontiguousarray(part)
+
+
+def run_gpu(w, x, chunk_sizes, n_streams, kind="device", flags=0, want_series=True,
+            chunk_len=None, trials=None):
+    ranges = w.ranges_array()
+    L = chunk_len or int(-(-max(chunk_sizes) // 256) * 256)
+    plan = dd.Plan(w.freqs(), w.tsamp, ranges, L, n_streams=n_streams, max_width=max(w.widths),
+                   peak_block=32, flags=flags)
+    out = []
+    T = 0
+    try:
+        for n in chunk_sizes:
+            buf = _as_input(x[T:T + n], kind)
+            seq = plan.run(buf, n)
+            plan.search(w.widths, w.threshold)
+            cands = plan.candidates(seq)
+            series = []
+            if want_series:
+                for r in range(len(ranges)):
+                    s, j0 = plan.series(r)
+                    s = s.cpu().numpy()
+                    if trials is not None:
+                        s = s[np.asarray(trials[r])]
+                    series.append((s, j0))
+            out.append((series, cands))
+            T += n
+        O = plan.O
+        shifts = plan.shifts
+    finally:
+        plan.close()
+    return out, O, shifts
+
+
+def check(w, x, chunk_sizes, n_streams, kind="device", trials=None):
+    ranges = w.ranges_array()
+    gpu, O, shifts = run_gpu(w, x, chunk_sizes, n_streams, kind, trials=trials)
+    ref = oracle.run(x, w.freqs(), w.tsamp, ranges, w.widths, w.threshold, 32, chunk_sizes,
+                     trials=trials)
+    assert O == ref["O"]
+    np.testing.assert_array_equal(shifts, np.concatenate(ref["tables"]))
+    nmatch = 0
+    for k, ((series, cands), per) in enumerate(zip(gpu, ref["chunks"])):
+        for r in range(len(ranges)):
+            s, j0 = series[r]
+            assert j0 == per[r]["J0"]
+            np.testing.assert_array_equal(s, per[r]["series"], err_msg=f"chunk {k} range {r}")
+        want = np.concatenate([per[r]["cands"] for r in range(len(ranges))])
+        got = cands
+        if trials is not None:
+            keep = np.zeros(got.size, bool)
+            for r in range(len(ranges)):
+                keep |= (got["range"] == r) & np.isin(got["trial"], trials[r])
+            got = got[keep]
+        d_of = lambda r: int(ranges[r][3])
+        J0_of = lambda r, per=per: per[r]["J0"]
+        tr_index = lambda r: {int(t): i for i, t in enumerate(per[r]["trials"])}
+        series_of = lambda r, t, per=per: per[r]["series"][tr_index(r)[t]]
+        nmatch += compare_candidates(got, want, w.threshold, 32, series_of, J0_of, d_of)
+    return nmatch
+
+
+# ----------------------------------------------------------------------------- tests
+
+def test_plan_matches_oracle_delay_table():
+    w = configs.mid(nsamp=1 << 16)
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 1 << 16, n_streams=1)
+    try:
+        tabs = oracle.shift_tables(w.freqs(), w.tsamp, w.ranges_array())
+        np.testing.assert_array_equal(plan.shifts, np.concatenate(tabs))
+        assert plan.O == oracle.overlap(tabs, w.ranges_array())
+    finally:
+        plan.close()
+
+
+def test_tiny_whole():
+    w = configs.tiny()
+    x = w.generate(_arrivals(w))
+    assert check(w, x, [w.nsamp], 1) > 0
+
+
+@pytest.mark.parametrize("n_streams", [1, 4])
+def test_tiny_chunked_streams(n_streams):
+    w = configs.tiny()
+    x = w.generate(_arrivals(w))
+    assert check(w, x, [8192] * 8, n_streams) > 0
+
+
+def _small_multirange(nchans=128, nsamp=1 << 15, npulses=6):
+    ranges = (configs.DMRange(0.0, 2.0, 40, 1), configs.DMRange(80.0, 4.0, 30, 2),
+              configs.DMRange(200.0, 5.0, 20, 4), configs.DMRange(300.0, 10.0, 18, 8))
+    w = configs.mid(nsamp=nsamp, chunk_len=4096, n_streams=3, npulses=npulses, nchans=4096,
+                    ranges=ranges, index=7)
+    w.nchans = nchans
+    w.foff = -300.0 / nchans
+    w.pulses = tuple(configs.PulseSpec(p.dm * 0.35, min(p.t_ref, nsamp - 6000), p.width,
+                                       p.amp * 4.0) for p in w.pulses)
+    return w
+
+
+def test_multirange_decimated_ragged_chunks():
+    w = _small_multirange()
+    x = w.generate(_arrivals(w))
+    sizes = [4096] * 7 + [2048, 2040]  # ragged tail chunks (multiples of d_max = 8)
+    assert sum(sizes) <= w.nsamp
+    assert check(w, x[:sum(sizes)], sizes, 3) > 0
+
+
+@pytest.mark.parametrize("kind", ["pinned", "pageable"])
+def test_ragged_channels_host_input(kind):
+    w = _small_multirange(nchans=98, nsamp=1 << 14, npulses=3)
+    x = w.generate(_arrivals(w))
+    check(w, x, [4096] * 4, 2, kind=kind)
+
+
+def test_input_kinds_give_identical_results():
+    w = _small_multirange(nsamp=1 << 14)
+    x = w.generate(_arrivals(w))
+    res = [run_gpu(w, x, [4096] * 4, 2, kind=k)[0] for k in ("device", "pinned", "pageable")]
+    for other in res[1:]:
+        for (sa, ca), (sb, cb) in zip(res[0], other):
+            np.testing.assert_array_equal(ca, cb)
+            for (a, _), (b, _) in zip(sa, sb):
+                np.testing.assert_array_equal(a, b)
+
+
+def test_pipelined_streams_match_sequential():
+    """Chunks enqueued back to back on 4 streams give the same candidates as one at a time."""
+    w = _small_multirange(nsamp=1 << 15)
+    x = w.generate(_arrivals(w))
+    sizes = [4096] * 8
+    seq_res = run_gpu(w, x, sizes, 1, want_series=False)[0]
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=4,
+                   max_width=max(w.widths))
+    xs = torch.from_numpy(x[:sum(sizes)]).cuda()
+    got = []
+    try:
+        for k in range(8):
+            plan.run(xs[4096 * k:4096 * (k + 1)], 4096)
+            plan.search(w.widths, w.threshold)
+            if k >= 3:
+                got.append(plan.candidates(k - 3))
+        for k in range(5, 8):
+            got.append(plan.candidates(k))
+    finally:
+        plan.close()
+    for (_, want), g in zip(seq_res, got):
+        np.testing.assert_array_equal(g, want)
+
+
+def test_first_chunk_shorter_than_overlap():
+    w = _small_multirange(nsamp=1 << 14)
+    x = w.generate(_arrivals(w))
+    tabs = oracle.shift_tables(w.freqs(), w.tsamp, w.ranges_array())
+    O = oracle.overlap(tabs, w.ranges_array())
+    first = (O // 2) // 8 * 8
+    sizes = [first, 4096, 4096]
+    check(w, x[:sum(sizes)], sizes, 2)
+
+
+def test_full_size_sampled_trials():
+    """4096 channels, 2^20 samples, 4050 trials, 8 chunks over 4 streams (the benchmark's
+    launch configuration); sampled trials of every range, every chunk, bit-exact series."""
+    w = configs.mid()
+    x = w.generate(_arrivals(w))
+    rng = np.random.default_rng(5)
+    trials = []
+    for r in w.ranges:
+        t = {0, r.n_trials - 1} | set(int(v) for v in rng.integers(0, r.n_trials, 2))
+        trials.append(sorted(t))
+    # also the trials nearest each injected pulse, so candidates are exercised
+    for p in w.pulses:
+        for ri, r in enumerate(w.ranges):
+            if r.dm_start <= p.dm < r.dm_start + r.n_trials * r.dm_step:
+                trials[ri] = sorted(set(trials[ri]) | {int((p.dm - r.dm_start) / r.dm_step)})
+    sizes = [w.chunk_len] * (w.nsamp // w.chunk_len)
+    assert check(w, x, sizes, w.n_streams, trials=trials) > 0
+
+
+def test_errors_are_reported():
+    w = _small_multirange(nsamp=1 << 13)
+    x = w.generate(_arrivals(w))
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=2,
+                   max_width=max(w.widths))
+    xs = torch.from_numpy(x).cuda()
+    try:
+        with pytest.raises(dd.DDError) as e:
+            plan.run(xs[:100], 100)  # not a multiple of the largest decimation
+        assert e.value.code == dd.DD_ERR_ARG
+        with pytest.raises(dd.DDError) as e:
+            dd.sps_run(plan.h, w.widths, w.threshold)  # nothing run yet
+        assert e.value.code == dd.DD_ERR_STATE
+        for k in range(3):
+            plan.run(xs[4096 * (k % 2):4096 * (k % 2 + 1)], 4096)
+            plan.search(w.widths, -1e30)  # every block is a candidate
+        with pytest.raises(dd.DDError) as e:
+            plan.search(w.widths, 6.0)
+        assert e.value.code == dd.DD_ERR_STATE
+        with pytest.raises(dd.DDError) as e:
+            plan.candidates(0)  # recycled by chunk 2 (2 streams)
+        assert e.value.code == dd.DD_ERR_STATE
+        full = plan.candidates(2)
+        assert full.size > 10
+        with pytest.raises(dd.DDError) as e:
+            plan.candidates(2, cap=5)
+        assert e.value.code == dd.DD_ERR_CAP
+        with pytest.raises(dd.DDError) as e:
+            plan.search([4, 2], 6.0)
+        assert e.value.code == dd.DD_ERR_ARG
+    finally:
+        plan.close()
+
+
+def test_timing_and_launch_counters():
+    w = _small_multirange(nsamp=1 << 14)
+    x = w.generate(_arrivals(w))
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=2,
+                   max_width=max(w.widths), flags=dd.DD_FLAG_TIMING)
+    try:
+        plan.stats(reset=True)
+        xs = torch.from_numpy(x).cuda()
+        for k in range(4):
+            plan.run(xs[4096 * k:4096 * (k + 1)], 4096)
+            plan.search(w.widths, w.threshold)
+        plan.sync()
+        launches, ms, nlaunch = plan.stats()
+        # every chunk: corner turn + 3 decimation levels; every range with a non-empty
+        # window: dedispersion (+ moments in the one-thread-per-output path) + search
+        windows = oracle.chunk_windows([4096] * 4, plan.O)
+        live = sum(1 for (_, _, lo, hi) in windows for r in w.ranges if hi // r.decimation >
+                   lo // r.decimation)
+        assert launches >= 4 * 4 + 2 * live
+        assert ms > 0 and nlaunch == live
+    finally:
+        plan.close()
