@@ -264,7 +264,7 @@ def main(args):
             pass
     dev = torch.cuda.current_device()
     dd.build()
-    w = configs.mid(beam=rank)
+    w = configs.mid(beam=rank, nsamp=args.nsamp, n_streams=args.streams)
     xh = make_input(w, pinned=True)
     xd = xh.cuda()
     L = w.chunk_len
@@ -304,7 +304,7 @@ def main(args):
                    "ranges": [[r.dm_start, r.dm_step, r.n_trials, r.decimation] for r in w.ranges],
                    "chunk_len": L, "chunks": nchunks, "n_streams": w.n_streams,
                    "widths": list(w.widths), "threshold": w.threshold, "overlap": O,
-                   "l2": "input 4.3 GB per step > L2 (no flush)"},
+                   "l2": f"input {w.nsamp * w.nchans / 1e9:.1f} GB per step > L2 (no flush)"},
         "real_time_factor": obs / (ms * 1e-3 / args.steps),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": w.nsamp * w.nchans,
                 "d2h_bytes_per_step": int(ncand_e2e / args.steps * 32 + nchunks * 8),
@@ -332,5 +332,8 @@ if __name__ == "__main__":
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nsamp", type=int, default=1 << 20,
+                    help="samples per beam (a multiple of 2^17; smaller only for profiler captures)")
+    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the chunks rotate over")
     a = ap.parse_args()
     sys.exit(main_reference(a) if a.impl == "reference" else main(a))

@@ -76,8 +76,8 @@ struct Slot {
   int32_t* series = nullptr;    // every range, at series_off[r]
   ddk::Moments* mom = nullptr;  // [total trials]
   dd_cand_t* cands = nullptr;   // [max_cands]
-  unsigned long long* d_count = nullptr;
-  unsigned long long* h_count = nullptr;  // pinned
+  unsigned long long* d_count = nullptr;  // [0] candidates, [1] kernel error bits
+  unsigned long long* h_count = nullptr;  // pinned copy of d_count
   cudaEvent_t ev_free = nullptr;          // last work enqueued for this slot
   cudaEvent_t ev_sps = nullptr;           // search + count readback done
   int64_t seq = -1, T = 0, n = 0, lo = 0, hi = 0;
@@ -85,6 +85,16 @@ struct Slot {
 };
 
 }  // namespace
+
+// How one range is dedispersed: the tiled DP4A kernel (with its tile shape and shared-memory
+// sizes) or, when the plan does not fit it, the one-thread-per-output kernel.
+struct RangeKernel {
+  bool tiled = false;
+  int tt = 0;
+  int row_slot = 0;
+  int zcap = 0;
+  size_t smem = 0;
+};
 
 struct dd_plan_s {
   int device = 0;
@@ -102,6 +112,7 @@ struct dd_plan_s {
   int64_t Rd[9] = {};
   std::vector<int64_t> series_off, series_stride;
   int64_t series_elems = 0;
+  std::vector<RangeKernel> rk;
   uint8_t* hist = nullptr;         // [C4][H] device history
   cudaEvent_t ev_hist = nullptr;
   std::vector<Slot> slots;
@@ -192,6 +203,61 @@ int timing_end(dd_plan_s* p, cudaStream_t st, int64_t slot) {
   if (slot < 0) return DD_OK;
   DD_CK(cudaEventRecord(p->tev[2 * slot + 1], st));
   return DD_OK;
+}
+
+// Size the tiled kernel for one range from its delay table [ntr][C4]: the largest delay spread
+// of a tile's trials in one channel (staged row length), and the largest number of pattern
+// words one stage of 4-channel groups needs (found exactly as the kernel finds them).
+RangeKernel plan_range_kernel(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
+  RangeKernel k;
+  const int D = ddk::tiled_trials_per_tile(), NG = ddk::tiled_groups_per_stage();
+  int64_t spread = 0, relmax = 0, zcap = 0;
+  for (int t0 = 0; t0 < ntr; t0 += D) {
+    const int n = std::min(D, ntr - t0);
+    for (int c = 0; c < c4; ++c) {
+      for (int i = 1; i < n; ++i)
+        if (tab[(int64_t)(t0 + i) * c4 + c] < tab[(int64_t)(t0 + i - 1) * c4 + c]) return k;
+      spread = std::max<int64_t>(spread, tab[(int64_t)(t0 + n - 1) * c4 + c] -
+                                             tab[(int64_t)t0 * c4 + c]);
+    }
+    for (int g0 = 0; g0 < c4 / 4; g0 += NG) {
+      int64_t stage = 0;
+      for (int g = g0; g < std::min(g0 + NG, c4 / 4); ++g) {
+        uint64_t key[64];
+        int bmin[64], bmax[64];
+        int np = 0;
+        for (int i = 0; i < n; ++i) {
+          const int32_t* s = tab + (int64_t)(t0 + i) * c4 + 4 * g;
+          const int b = std::min(std::min(s[0], s[1]), std::min(s[2], s[3]));
+          uint64_t kk = 0;
+          for (int q = 0; q < 4; ++q) {
+            relmax = std::max<int64_t>(relmax, s[q] - b);
+            kk |= (uint64_t)(uint32_t)(s[q] - b) << (16 * q);
+          }
+          int p = 0;
+          while (p < np && key[p] != kk) ++p;
+          if (p == np) {
+            key[np] = kk;
+            bmin[np] = bmax[np] = b;
+            ++np;
+          } else {
+            bmin[p] = std::min(bmin[p], b);
+            bmax[p] = std::max(bmax[p], b);
+          }
+        }
+        for (int p = 0; p < np; ++p) stage += tt + bmax[p] - bmin[p];
+      }
+      zcap = std::max(zcap, stage);
+    }
+  }
+  if (relmax >= 65536 || spread > 65536) return k;
+  const int A = u16 ? 8 : 16;
+  k.tt = tt;
+  k.row_slot = (int)round_up(tt + spread + 2 * A, A);
+  k.zcap = (int)round_up(std::max<int64_t>(zcap, 1), 4);
+  k.smem = ddk::tiled_smem_bytes(u16, k.row_slot, k.zcap);
+  k.tiled = k.smem <= 200 * 1024;
+  return k;
 }
 
 }  // namespace
@@ -335,12 +401,32 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
       need = std::max<int64_t>(need, smax * ranges[r].decimation);
     }
     p->O = round_up(need, dmax);
+    p->rk.resize(nranges);
+    if (!(o.flags & DD_FLAG_NAIVE)) {
+      for (int r = 0; r < nranges; ++r) {
+        const bool u16 = ranges[r].decimation > 1;
+        for (int tt : {u16 ? 512 : 1024, u16 ? 256 : 512}) {
+          RangeKernel k = plan_range_kernel(&full[(size_t)p->row0[r] * p->C4], ranges[r].n_trials,
+                                            p->C4, u16, tt);
+          if (k.tiled) {
+            cudaError_t e2 = ddk::prepare_tiled(u16, tt, k.smem);
+            if (e2 != cudaSuccess) {
+              free_plan(p);
+              return fail(DD_ERR_CUDA, "tiled kernel set-up: %s", cudaGetErrorString(e2));
+            }
+            p->rk[r] = k;
+            break;
+          }
+        }
+      }
+    }
   }
   // history kept on the device: O rounded up so every ring row starts 256-byte aligned
   p->H = round_up(p->O, 256);
   const int64_t span = p->H + p->L;
-  p->R1 = round_up(span, 256) + 256;
-  for (int l = 1; l <= p->levels; ++l) p->Rd[l] = round_up(span >> l, 128) + 128;
+  // rows carry slack past the data so a ragged last time tile may stage (and ignore) a full tile
+  p->R1 = round_up(span, 256) + 2048;
+  for (int l = 1; l <= p->levels; ++l) p->Rd[l] = round_up(span >> l, 128) + 2048;
   p->series_off.resize(nranges);
   p->series_stride.resize(nranges);
   int64_t off = 0;
@@ -379,8 +465,9 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     DD_TRY(dalloc(&s.series, sizeof(int32_t) * (size_t)p->series_elems, "series"));
     DD_TRY(dalloc(&s.mom, sizeof(ddk::Moments) * (size_t)total_rows, "moments"));
     DD_TRY(dalloc(&s.cands, sizeof(dd_cand_t) * (size_t)p->opts.max_cands, "candidates"));
-    DD_TRY(dalloc(&s.d_count, sizeof(unsigned long long), "count"));
-    if (cudaMallocHost((void**)&s.h_count, sizeof(unsigned long long)) != cudaSuccess) {
+    DD_TRY(dalloc(&s.d_count, 2 * sizeof(unsigned long long), "count"));
+    DD_TRYCK(cudaMemset(s.d_count, 0, 2 * sizeof(unsigned long long)));
+    if (cudaMallocHost((void**)&s.h_count, 2 * sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       s.h_count = nullptr;
       free_plan(p);
@@ -447,6 +534,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
   }
   const int64_t T = p->T_total;
   const int64_t lo = std::max<int64_t>(0, T - p->O), hi = std::max<int64_t>(0, T + nsamp - p->O);
+  if (hi > lo) DD_CK(cudaMemsetAsync(s.mom, 0, sizeof(ddk::Moments) * p->total_rows, st));
   for (size_t r = 0; r < p->ranges.size(); ++r) {
     const int d = p->ranges[r].decimation;
     const int l = ilog2(d);
@@ -465,11 +553,33 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
     int64_t ts;
     int rc = timing_begin(p, st, &ts);
     if (rc) return rc;
-    DD_CK(ddk::launch_dedisp_naive(R, p->C4, st));
+    const RangeKernel& K = p->rk[r];
+    if (K.tiled) {
+      ddk::TiledArgs A;
+      A.xd = R.xd;
+      A.xd_stride = R.xd_stride;
+      A.m0 = R.m0;
+      A.nout = R.nout;
+      A.y = R.y;
+      A.y_stride = R.y_stride;
+      A.mom = R.mom;
+      A.shifts = R.shifts;
+      A.n_trials = R.n_trials;
+      A.c4 = p->C4;
+      A.row_slot = K.row_slot;
+      A.zcap = K.zcap;
+      A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
+      DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, st));
+      p->launches += 1;
+    } else {
+      DD_CK(ddk::launch_dedisp_naive(R, p->C4, st));
+    }
     rc = timing_end(p, st, ts);
     if (rc) return rc;
-    DD_CK(ddk::launch_moments(R.y, R.n_trials, R.nout, R.y_stride, R.mom, st));
-    p->launches += 2;
+    if (!K.tiled) {
+      DD_CK(ddk::launch_moments(R.y, R.n_trials, R.nout, R.y_stride, R.mom, st));
+      p->launches += 2;
+    }
   }
   DD_CK(cudaEventRecord(s.ev_free, st));
   s.used = st;
@@ -540,8 +650,8 @@ int sps_run(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold
     DD_CK(ddk::launch_sps(a, st));
     p->launches += 1;
   }
-  DD_CK(cudaMemcpyAsync(s.h_count, s.d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                        st));
+  DD_CK(cudaMemcpyAsync(s.h_count, s.d_count, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, st));
   DD_CK(cudaEventRecord(s.ev_sps, st));
   DD_CK(cudaEventRecord(s.ev_free, st));
   s.searched = true;
@@ -562,7 +672,10 @@ int dd_candidates(dd_plan_t p, int64_t seq, dd_cand_t* out, int64_t cap, int64_t
   DD_CK(cudaSetDevice(p->device));
   int rc = wait_event(s.ev_sps, timeout_ms);
   if (rc) return rc;
-  const int64_t count = (int64_t)*s.h_count;
+  if (s.h_count[1] != 0)
+    return fail(DD_ERR_TIMEOUT, "a dedispersion kernel stopped early (error bits %llu)",
+                (unsigned long long)s.h_count[1]);
+  const int64_t count = (int64_t)s.h_count[0];
   const int64_t kept = std::min<int64_t>(count, p->opts.max_cands);
   if (kept > 0) {
     DD_CK(cudaStreamWaitEvent(p->io, s.ev_sps, 0));

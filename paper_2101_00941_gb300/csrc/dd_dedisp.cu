@@ -116,40 +116,46 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Issue the bulk copies of one stage's channel rows (single thread).
+// Delays bounding one stage's channel rows for this tile: lane k < kRows loads the first and the
+// last trial's delay of channel stage*kRows + k (delays are non-decreasing in the trial index).
+__device__ __forceinline__ void stage_bounds(const TiledArgs& a, int stage, int lane, int trial0,
+                                             int ntr, int& smin, int& smax) {
+  const int c = stage * kRows + lane;
+  smin = smax = 0;
+  if (lane < kRows && c < a.c4) {
+    smin = __ldg(a.shifts + (int64_t)trial0 * a.c4 + c);
+    smax = __ldg(a.shifts + (int64_t)(trial0 + ntr - 1) * a.c4 + c);
+  }
+}
+
+// Warp-cooperative issue of one stage: lane k copies channel row k with one bulk (TMA) copy of
+// whole 16-byte units covering [m0 + j0 + smin, m0 + j0 + smax + TT); lane 0 first arms the
+// stage's mbarrier with the total byte count.
 template <typename T, int TT>
 __device__ void issue_stage(const TiledArgs& a, int stage, T* raw_buf, unsigned long long* bar,
-                            int trial0, int ntr, int64_t j0) {
+                            int64_t j0, int lane, int smin, int smax) {
   constexpr int A = 16 / (int)sizeof(T);  // elements per 16 bytes
-  const int cbeg = stage * kRows;
-  const int nch = min(kRows, a.c4 - cbeg);
-  const T* xd = static_cast<const T*>(a.xd);
-  int64_t a0[kRows];
-  uint32_t nb[kRows];
-  uint32_t total = 0;
-#pragma unroll
-  for (int k = 0; k < kRows; ++k) {
-    nb[k] = 0;
-    a0[k] = 0;
-    if (k < nch) {
-      const int c = cbeg + k;
-      const int32_t smin = a.shifts[(int64_t)trial0 * a.c4 + c];
-      const int32_t smax = a.shifts[(int64_t)(trial0 + ntr - 1) * a.c4 + c];
-      const int64_t start = a.m0 + j0 + smin;
-      a0[k] = start & ~(int64_t)(A - 1);
-      const int64_t end = a.m0 + j0 + smax + TT;
-      nb[k] = (uint32_t)(((end - a0[k]) * (int64_t)sizeof(T) + 15) & ~int64_t(15));
-      total += nb[k];
-    }
+  const int c = stage * kRows + lane;
+  const bool mine = lane < kRows && c < a.c4;
+  int64_t a0 = 0;
+  uint32_t nb = 0;
+  if (mine) {
+    const int64_t start = a.m0 + j0 + smin;
+    a0 = start & ~(int64_t)(A - 1);
+    const int64_t end = a.m0 + j0 + smax + TT;
+    nb = (uint32_t)(((end - a0) * (int64_t)sizeof(T) + 15) & ~int64_t(15));
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_arrive_expect_tx(bar, total);
+  uint32_t total = nb;
 #pragma unroll
-  for (int k = 0; k < kRows; ++k) {
-    if (k < nch)
-      bulk_g2s(raw_buf + (size_t)k * a.row_slot, xd + (int64_t)(cbeg + k) * a.xd_stride + a0[k],
-               nb[k], bar);
+  for (int off = 16; off > 0; off >>= 1) total += __shfl_xor_sync(0xffffffffu, total, off);
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(bar, total);
   }
+  __syncwarp();
+  if (mine)
+    bulk_g2s(raw_buf + (size_t)lane * a.row_slot,
+             static_cast<const T*>(a.xd) + (int64_t)c * a.xd_stride + a0, nb, bar);
 }
 
 template <typename T>
@@ -207,12 +213,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
+  // warp 0 issues stages 0 .. kNStage-2 now and stage s + kNStage - 1 during stage s, using
+  // delays it loaded one stage earlier (so the loads' latency overlaps the previous stage)
   int issued = 0;
-  if (tid == 0) {
+  int nx_min = 0, nx_max = 0;  // bounds of the next stage to issue (warp 0)
+  if (warp == 0) {
     for (int s = 0; s < kNStage - 1 && s < nstages; ++s) {
-      issue_stage<T, TT>(a, s, raw + (size_t)s * stage_elems, &mbar[s], trial0, ntr, j0);
+      int smin, smax;
+      stage_bounds(a, s, lane, trial0, ntr, smin, smax);
+      issue_stage<T, TT>(a, s, raw + (size_t)s * stage_elems, &mbar[s], j0, lane, smin, smax);
       ++issued;
     }
+    if (kNStage - 1 < nstages) stage_bounds(a, kNStage - 1, lane, trial0, ntr, nx_min, nx_max);
   }
 
   uint32_t acc[kTPW][KT];
@@ -222,15 +234,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
     for (int k = 0; k < KT; ++k) acc[q][k] = 0;
 
   bool aborted = false;
+  int s_abort = 0;
   for (int s = 0; s < nstages; ++s) {
     const int buf = s % kNStage;
     const int db = s & 1;
     const int ng = min(kNG, ngroups - s * kNG);
-    if (tid == 0 && s + kNStage - 1 < nstages) {
+    if (warp == 0 && s + kNStage - 1 < nstages) {
       const int s2 = s + kNStage - 1;
-      issue_stage<T, TT>(a, s2, raw + (size_t)(s2 % kNStage) * stage_elems,
-                         &mbar[s2 % kNStage], trial0, ntr, j0);
+      issue_stage<T, TT>(a, s2, raw + (size_t)(s2 % kNStage) * stage_elems, &mbar[s2 % kNStage],
+                         j0, lane, nx_min, nx_max);
       ++issued;
+      if (s2 + 1 < nstages) stage_bounds(a, s2 + 1, lane, trial0, ntr, nx_min, nx_max);
     }
     // ---- relative-delay patterns of each 4-channel group (one warp per group)
     if (warp < ng) {
@@ -294,6 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
     if (!aborted) ok = mbar_wait_bounded(&mbar[buf], (uint32_t)((s / kNStage) & 1));
     if (__syncthreads_or(!ok)) {
       aborted = true;
+      s_abort = s;
       break;
     }
     // ---- build the pattern words
@@ -307,6 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
     if (ztotal > a.zcap) {  // cannot happen for a table the host sized; refuse, never overflow
       if (tid == 0) atomicOr(a.err, 2);
       aborted = true;
+      s_abort = s + 1;  // this stage's copies have landed
       break;
     }
     const T* rawb = raw + (size_t)buf * stage_elems;
@@ -347,8 +363,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
   if (aborted) {
     if (tid == 0) {
       atomicOr(a.err, 1);
-      // let every copy already issued land before the CTA's shared memory goes away
-      for (int s = 0; s < issued; ++s) mbar_wait_bounded(&mbar[s % kNStage], (s / kNStage) & 1);
+      // let every copy still in flight land before the CTA's shared memory goes away
+      for (int s = s_abort; s < issued; ++s)
+        mbar_wait_bounded(&mbar[s % kNStage], (uint32_t)((s / kNStage) & 1));
     }
     return;
   }
@@ -401,10 +418,17 @@ cudaError_t launch_tiled_t(const TiledArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Ranges sharing an instance need different amounts of shared memory, so the instance is
+// allowed the device's opt-in maximum once (a launch still only reserves what it asks for).
 template <typename T, int TT>
 cudaError_t prepare_t(size_t smem) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(k_dedisp_tiled<T, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+                              optin);
 }
 
 }  // namespace

@@ -65,6 +65,29 @@ struct DedispRange {
   int32_t is_u16;
 };
 
+// Arguments of the tiled dedispersion kernel (dd_dedisp.cu), one launch per range.
+struct TiledArgs {
+  const void* xd;          // decimated ring, uint8 (d == 1) or uint16, [C4][xd_stride]
+  int64_t xd_stride;       // elements
+  int64_t m0;              // ring column of window sample 0
+  int64_t nout;            // window length
+  int32_t* y;              // [n_trials][y_stride]
+  int64_t y_stride;
+  Moments* mom;            // [n_trials], zeroed before the launch
+  const int32_t* shifts;   // [n_trials][C4], non-decreasing in the trial index
+  int32_t n_trials;
+  int32_t c4;
+  int32_t row_slot;        // elements per staged channel row
+  int32_t zcap;            // pattern words per stage
+  int32_t* err;            // bit 0: a bounded wait ran out; bit 1: pattern buffer too small
+};
+
+int tiled_trials_per_tile();
+int tiled_groups_per_stage();
+size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap);
+cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
+cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st);
+
 // ---- launchers (dd_kernels.cu); each returns the cudaGetLastError() of its launch
 cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t c4, double fref,
                                double tsamp, const ShiftRange* ranges, int32_t nranges,

@@ -70,9 +70,9 @@ def run_gpu(w, x, chunk_sizes, n_streams, kind="device", flags=0, want_series=Tr
     return out, O, shifts
 
 
-def check(w, x, chunk_sizes, n_streams, kind="device", trials=None):
+def check(w, x, chunk_sizes, n_streams, kind="device", trials=None, flags=0):
     ranges = w.ranges_array()
-    gpu, O, shifts = run_gpu(w, x, chunk_sizes, n_streams, kind, trials=trials)
+    gpu, O, shifts = run_gpu(w, x, chunk_sizes, n_streams, kind, trials=trials, flags=flags)
     ref = oracle.run(x, w.freqs(), w.tsamp, ranges, w.widths, w.threshold, 32, chunk_sizes,
                      trials=trials)
     assert O == ref["O"]
@@ -142,6 +142,13 @@ def test_multirange_decimated_ragged_chunks():
     sizes = [4096] * 7 + [2048, 2040]  # ragged tail chunks (multiples of d_max = 8)
     assert sum(sizes) <= w.nsamp
     assert check(w, x[:sum(sizes)], sizes, 3) > 0
+
+
+def test_one_thread_per_output_kernel_matches():
+    """The testing-aid kernel (DD_FLAG_NAIVE) obeys the same contract as the tiled one."""
+    w = _small_multirange(nsamp=1 << 14)
+    x = w.generate(_arrivals(w))
+    check(w, x, [4096] * 4, 2, flags=dd.DD_FLAG_NAIVE)
 
 
 @pytest.mark.parametrize("kind", ["pinned", "pageable"])
