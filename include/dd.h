@@ -168,8 +168,10 @@ int dd_sync(dd_plan_t plan);
 /*
  * dd_stats -- counters of the plan since creation or the last reset.
  *   launches      : kernels launched by the plan
- *   dedisp_ms     : summed device time of the dedispersion launches (needs DD_FLAG_TIMING;
- *                   measured with CUDA events on the launching stream; complete after dd_sync)
+ *   dedisp_ms     : device time during which at least one dedispersion launch was running (the
+ *                   union of the launches' intervals, so launches of chunks that overlap on
+ *                   different streams count once); needs DD_FLAG_TIMING; measured with CUDA
+ *                   events on each launching stream; complete after dd_sync
  *   dedisp_launches : dedispersion launches timed
  *   reset         : non-zero = zero the counters after reading
  */

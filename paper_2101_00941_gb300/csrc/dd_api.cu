@@ -121,9 +121,14 @@ struct dd_plan_s {
   dd_cand_t* h_cands = nullptr;    // pinned [max_cands]
   int64_t next_seq = 0, T_total = 0;
   int64_t launches = 0;
-  // dedispersion timing (DD_FLAG_TIMING)
+  // dedispersion timing (DD_FLAG_TIMING): every launch is bracketed by an event pair; the pairs
+  // are turned into [start, end) intervals against a common reference event and merged, so that
+  // launches of different chunks running at the same time on different streams count once
   std::vector<cudaEvent_t> tev;
   int64_t tev_used = 0;
+  cudaEvent_t tref = nullptr;
+  bool tref_set = false;
+  std::vector<std::pair<double, double>> intervals;
   double dedisp_ms = 0;
   int64_t dedisp_launches = 0;
 };
@@ -151,6 +156,7 @@ void free_plan(dd_plan_s* p) {
     if (s.stream) cudaStreamDestroy(s.stream);
   }
   for (auto e : p->tev) cudaEventDestroy(e);
+  if (p->tref) cudaEventDestroy(p->tref);
   cudaFree(p->d_shifts);
   cudaFree(p->hist);
   cudaFreeHost(p->h_cands);
@@ -171,27 +177,47 @@ int dalloc(T** ptr, size_t bytes, const char* what) {
   return DD_OK;
 }
 
-// Harvest finished timing event pairs into the running total (all of them if `all`).
-int harvest_timing(dd_plan_s* p, bool all) {
+// Turn recorded event pairs into intervals relative to the reference event.
+int harvest_timing(dd_plan_s* p) {
   for (int64_t k = 0; k < p->tev_used; ++k) {
     cudaEvent_t a = p->tev[2 * k], b = p->tev[2 * k + 1];
-    if (all) {
-      DD_CK(cudaEventSynchronize(b));
-    }
-    float ms = 0;
-    DD_CK(cudaEventElapsedTime(&ms, a, b));
-    p->dedisp_ms += ms;
+    DD_CK(cudaEventSynchronize(b));
+    float t0 = 0, t1 = 0;
+    DD_CK(cudaEventElapsedTime(&t0, p->tref, a));
+    DD_CK(cudaEventElapsedTime(&t1, p->tref, b));
+    p->intervals.emplace_back(t0, t1);
     p->dedisp_launches += 1;
   }
   p->tev_used = 0;
   return DD_OK;
 }
 
+// Length of the union of the harvested intervals (ms).
+double union_ms(std::vector<std::pair<double, double>> v) {
+  std::sort(v.begin(), v.end());
+  double total = 0, cs = 0, ce = -1e300;
+  for (auto& iv : v) {
+    if (iv.first > ce) {
+      if (ce > cs) total += ce - cs;
+      cs = iv.first;
+      ce = iv.second;
+    } else if (iv.second > ce) {
+      ce = iv.second;
+    }
+  }
+  if (ce > cs) total += ce - cs;
+  return total;
+}
+
 int timing_begin(dd_plan_s* p, cudaStream_t st, int64_t* slot) {
   *slot = -1;
   if (!(p->opts.flags & DD_FLAG_TIMING)) return DD_OK;
+  if (!p->tref_set) {
+    DD_CK(cudaEventRecord(p->tref, st));
+    p->tref_set = true;
+  }
   if (2 * (p->tev_used + 1) > (int64_t)p->tev.size()) {
-    int rc = harvest_timing(p, true);
+    int rc = harvest_timing(p);
     if (rc) return rc;
   }
   *slot = p->tev_used++;
@@ -477,6 +503,8 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
   if (o.flags & DD_FLAG_TIMING) {
     p->tev.resize(2 * 1024);
     for (auto& e : p->tev) DD_TRYCK(cudaEventCreate(&e));
+    DD_TRYCK(cudaEventCreate(&p->tref));
+    p->intervals.reserve(1 << 16);
   }
   DD_TRYCK(cudaDeviceSynchronize());
 #undef DD_TRY
@@ -714,15 +742,18 @@ int dd_stats(dd_plan_t p, int64_t* launches, double* dedisp_ms, int64_t* dedisp_
              int32_t reset) {
   if (!p) return fail(DD_ERR_ARG, "plan is NULL");
   DD_CK(cudaSetDevice(p->device));
-  int rc = harvest_timing(p, true);
-  if (rc) return rc;
+  if (p->tref_set) {
+    int rc = harvest_timing(p);
+    if (rc) return rc;
+  }
   if (launches) *launches = p->launches;
-  if (dedisp_ms) *dedisp_ms = p->dedisp_ms;
+  if (dedisp_ms) *dedisp_ms = union_ms(p->intervals);
   if (dedisp_launches) *dedisp_launches = p->dedisp_launches;
   if (reset) {
     p->launches = 0;
-    p->dedisp_ms = 0;
+    p->intervals.clear();
     p->dedisp_launches = 0;
+    p->tref_set = false;  // the next launch records a fresh reference
   }
   return DD_OK;
 }
