@@ -249,8 +249,8 @@ RangeKernel plan_range_kernel(const int32_t* tab, int ntr, int c4, bool u16, int
     for (int g0 = 0; g0 < c4 / 4; g0 += NG) {
       int64_t stage = 0;
       for (int g = g0; g < std::min(g0 + NG, c4 / 4); ++g) {
-        uint64_t key[64];
-        int bmin[64], bmax[64];
+        uint64_t key[256];
+        int bmin[256], bmax[256];
         int np = 0;
         for (int i = 0; i < n; ++i) {
           const int32_t* s = tab + (int64_t)(t0 + i) * c4 + 4 * g;
@@ -271,7 +271,13 @@ RangeKernel plan_range_kernel(const int32_t* tab, int ntr, int c4, bool u16, int
             bmax[p] = std::max(bmax[p], b);
           }
         }
-        for (int p = 0; p < np; ++p) stage += tt + bmax[p] - bmin[p];
+        int items = 0;
+        for (int p = 0; p < np; ++p) {
+          const int zl = (tt + bmax[p] - bmin[p] + 3) & ~3;
+          stage += zl;
+          items += (zl / (u16 ? 2 : 4) + 31) / 32;
+        }
+        if (items > 128 || np > 255) return k;  // the kernel's per-group item table
       }
       zcap = std::max(zcap, stage);
     }
@@ -279,7 +285,9 @@ RangeKernel plan_range_kernel(const int32_t* tab, int ntr, int c4, bool u16, int
   if (relmax >= 65536 || spread > 65536) return k;
   const int A = u16 ? 8 : 16;
   k.tt = tt;
-  k.row_slot = (int)round_up(tt + spread + 2 * A, A);
+  // staged row: up to A-1 elements of alignment in front, 16-byte rounding behind, and 16
+  // elements the word-wise pattern build may read past the last word it uses
+  k.row_slot = (int)round_up(tt + spread + 2 * A + 16, A);
   k.zcap = (int)round_up(std::max<int64_t>(zcap, 1), 4);
   k.smem = ddk::tiled_smem_bytes(u16, k.row_slot, k.zcap);
   k.tiled = k.smem <= 200 * 1024;
@@ -431,7 +439,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     if (!(o.flags & DD_FLAG_NAIVE)) {
       for (int r = 0; r < nranges; ++r) {
         const bool u16 = ranges[r].decimation > 1;
-        for (int tt : {u16 ? 512 : 1024, u16 ? 256 : 512}) {
+        for (int tt : {ddk::tiled_tile_samples(u16, 0), ddk::tiled_tile_samples(u16, 1)}) {
           RangeKernel k = plan_range_kernel(&full[(size_t)p->row0[r] * p->C4], ranges[r].n_trials,
                                             p->C4, u16, tt);
           if (k.tiled) {

@@ -83,6 +83,7 @@ struct TiledArgs {
 };
 
 int tiled_trials_per_tile();
+int tiled_tile_samples(int is_u16, int choice);
 int tiled_groups_per_stage();
 size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap);
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
