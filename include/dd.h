@@ -178,6 +178,39 @@ int dd_sync(dd_plan_t plan);
 int dd_stats(dd_plan_t plan, int64_t* launches, double* dedisp_ms, int64_t* dedisp_launches,
              int32_t reset);
 
+/*
+ * dd_sps_static -- the single pulse search of dd_candidates, on caller-provided device series,
+ * with no memory allocated by the library. The paper has no counterpart: this entry point exists
+ * for callers that cannot let a library allocate device memory at run time -- a real-time
+ * pipeline that reserves its whole GPU memory budget at start-up and must never take the
+ * implicit synchronisation of cudaMalloc/cudaFree in its processing loop, or a plug-in whose
+ * host framework owns every device allocation.
+ *   series     : DEVICE int32 [n_trials][stride], window samples 0..n-1 of one range
+ *                (e.g. from dd_series); read-only
+ *   n_trials   : 1 .. 16384 (the capacity of the fixed scratch; larger counts are rejected)
+ *   range, decimation, j0 : copied into the candidates (range index, d_r, global decimated
+ *                index of window sample 0), exactly as the plan's search reports them
+ *   widths, nwidths, threshold, peak_block : as in sps_run / dd_opts_t (widths on the HOST)
+ *   cands      : DEVICE dd_cand_t [cap], caller-owned; filled in no particular order
+ *   count      : DEVICE unsigned long long, caller-owned; set to the number of candidates
+ *                found (entries beyond cap are counted but not written)
+ *   cuda_stream: cudaStream_t the work is enqueued on (NULL = the default stream); returns
+ *                without waiting
+ * Scratch: per-trial moments in a fixed device array of 16384 records (512 KB), which every GPU
+ * that loads the library holds until the process exits. The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current, so make the
+ * first call on each device before any stream capture. Every call shares the array and leaves
+ * its contents behind: calls whose work may overlap on the GPU (different streams, or several
+ * host threads) race on it and must be serialised by the caller. The count is cleared by the
+ * call; the moments are recomputed in full.
+ * Errors (dd_last_error explains): DD_ERR_ARG (NULL pointer, sizes outside the limits above,
+ * bad widths), DD_ERR_CUDA (no device or a failed launch).
+ */
+int dd_sps_static(const int32_t* series, int32_t n_trials, int64_t n, int64_t stride,
+                  int32_t range, int32_t decimation, int64_t j0, const int32_t* widths,
+                  int32_t nwidths, float threshold, int32_t peak_block, dd_cand_t* cands,
+                  int64_t cap, unsigned long long* count, void* cuda_stream);
+
 /* dd_plan_destroy -- wait for the plan's work and free everything it allocated. NULL is a no-op. */
 void dd_plan_destroy(dd_plan_t plan);
 

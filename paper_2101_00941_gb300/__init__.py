@@ -26,7 +26,7 @@ DD_FLAG_TIMING = 1
 DD_FLAG_NAIVE = 2
 
 EXPORTS = ("dd_plan", "dd_plan_info", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
-           "dd_stats", "dd_plan_destroy", "dd_last_error")
+           "dd_stats", "dd_sps_static", "dd_plan_destroy", "dd_last_error")
 
 
 class dd_range_t(ctypes.Structure):
@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
         L.dd_candidates.argtypes = [vp, i64, vp, i64, P(i64), i64]
         L.dd_sync.argtypes = [vp]
         L.dd_stats.argtypes = [vp, P(i64), P(f64), P(i64), i32]
+        L.dd_sps_static.argtypes = [vp, i32, i64, i64, i32, i32, i64, vp, i32, f32, i32, vp, i64,
+                                    vp, vp]
         L.dd_plan_destroy.argtypes = [vp]
         L.dd_plan_destroy.restype = None
         L.dd_last_error.argtypes = []
@@ -164,6 +166,17 @@ def dd_stats(plan: int, reset: bool = False):
     a, b, c = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
     _check(lib().dd_stats(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(reset)))
     return a.value, b.value, c.value
+
+
+def dd_sps_static(series_ptr: int, n_trials: int, n: int, stride: int, range_idx: int,
+                  decimation: int, j0: int, widths, threshold: float, peak_block: int,
+                  cands_ptr: int, cap: int, count_ptr: int, cuda_stream: int = 0):
+    """Search device series with the library's fixed scratch (no allocation); see dd.h."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    _check(lib().dd_sps_static(int(series_ptr), int(n_trials), int(n), int(stride),
+                               int(range_idx), int(decimation), int(j0), w.ctypes.data, w.size,
+                               ctypes.c_float(threshold), int(peak_block), int(cands_ptr),
+                               int(cap), int(count_ptr), int(cuda_stream) or None))
 
 
 def dd_plan_destroy(plan: int):

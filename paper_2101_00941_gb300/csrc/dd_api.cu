@@ -296,6 +296,10 @@ RangeKernel plan_range_kernel(const int32_t* tab, int ntr, int c4, bool u16, int
 
 }  // namespace
 
+namespace ddk {
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace ddk
+
 extern "C" {
 
 const char* dd_last_error(void) { return g_err.c_str(); }

@@ -89,6 +89,9 @@ size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap);
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st);
 
+// Record `msg` as the calling thread's last error (dd_last_error) and return `code`.
+int report_error(int code, const char* msg);
+
 // ---- launchers (dd_kernels.cu); each returns the cudaGetLastError() of its launch
 cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t c4, double fref,
                                double tsamp, const ShiftRange* ranges, int32_t nranges,
