@@ -294,14 +294,39 @@ __device__ __forceinline__ double u128_to_f64(unsigned long long hi, unsigned lo
 constexpr int kSpsThreads = 256;
 constexpr int kSpsSeg = 1024;  // window samples per pass
 
+// Largest value of v over the block of B lanes holding `lane` (B a power of two <= 32).
+__device__ __forceinline__ uint32_t block_max(uint32_t v, int B) {
+  if (B == 32) return __reduce_max_sync(0xffffffffu, v);
+  for (int o = B >> 1; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Exact argmax over the block: largest v among valid lanes, ties to the lowest lane. Returns
+// -1 when the block has no valid lane; `off` = lane offset within the block.
+__device__ __forceinline__ int block_argmax(uint32_t v, bool valid, int B, int lane, int& off) {
+  unsigned long long key =
+      valid ? (((unsigned long long)v << 32) | (0xFFFFFFFFu - (uint32_t)(lane & (B - 1)))) : 0ull;
+  for (int o = B >> 1; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, key, o);
+    key = t > key ? t : key;
+  }
+  off = key ? (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu)) : 0;
+  return key ? (int)(key >> 32) : -1;
+}
+
+// One CTA per trial. Each pass covers kSpsSeg window samples plus `hist` samples before them:
+// a uint32 prefix sum in shared memory gives every boxcar exactly (boxcar sums are < 2^31, so
+// the difference of two wrapped prefixes is exact). Per block of B samples and per width the
+// block maximum of the boxcar sum is compared with an integer bound below which the SNR cannot
+// reach the threshold; only blocks that pass run the exact argmax and the FP64 SNR.
 __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
-  extern __shared__ long long P[];  // [1 + hist + kSpsSeg]: P[0] = 0, P[1+u] = sum_{k<=u}
+  extern __shared__ uint32_t P[];  // [1 + hist + kSpsSeg]: P[0] = 0, P[1+u] = sum_{k<=u} mod 2^32
   __shared__ double den[kMaxWidths];
-  __shared__ float inv32[kMaxWidths];
-  __shared__ long long warp_tot[kSpsThreads / 32];
+  __shared__ long long bthr[kMaxWidths];
+  __shared__ uint32_t warp_tot[kSpsThreads / 32];
 
   const int32_t i = blockIdx.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const Moments m = a.mom[i];
   const long long n = a.n;
   if (n <= 0) return;
@@ -316,118 +341,109 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
   const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
   if (v_lo == 0 && v_hi == 0) return;  // constant series: no candidates
   const double sq = sqrt(u128_to_f64(v_hi, v_lo));
+  const double thr = (double)a.threshold;
   if (tid < a.nw) {
-    den[tid] = sqrt((double)a.wd[tid]) * sq;
-    inv32[tid] = (float)(1.0 / den[tid]);
+    const int w = a.wd[tid];
+    den[tid] = sqrt((double)w) * sq;
+    // SNR >= thr  <=>  B >= (w*S1 + thr*den) / n; the bound keeps a margin of 2 + 1e-9 relative
+    // so that rounding in this estimate can never reject a block the exact test accepts
+    const double t = ((double)w * (double)s1 + thr * den[tid]) / (double)n;
+    const double tl = t - 2.0 - 1e-9 * fabs(t);
+    bthr[tid] = tl < -4e18 ? -(1ll << 62) : (tl > 4e18 ? (1ll << 62) : (long long)floor(tl));
   }
   const int H = a.hist;
   const int span = H + kSpsSeg;
   const int E = span / kSpsThreads;  // entries per thread in the scan (span % 256 == 0)
   const int32_t* yi = a.y + (int64_t)i * a.stride;
   const int B = a.block;
-  const float thr = a.threshold;
-  const float margin = 1e-3f * fmaxf(1.0f, fabsf(thr));
   if (tid == 0) P[0] = 0;
 
   for (long long seg0 = 0; seg0 < n; seg0 += kSpsSeg) {
     // ---- prefix sums of y[seg0-H .. seg0+kSpsSeg), zero outside the window
-    long long run = 0;
-    long long vals[8];
+    uint32_t run = 0;
+    uint32_t vals[8];
     const long long base = seg0 - H + (long long)tid * E;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       if (e < E) {
         const long long k = base + e;
-        run += (k >= 0 && k < n) ? (long long)yi[k] : 0ll;
+        run += (k >= 0 && k < n) ? (uint32_t)yi[k] : 0u;
         vals[e] = run;
       }
     }
-    // exclusive scan of per-thread totals
-    long long incl = run;
-    const int lane = tid & 31, wid = tid >> 5;
+    uint32_t incl = run;
+#pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const long long o = __shfl_up_sync(0xffffffffu, incl, off);
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
       if (lane >= off) incl += o;
     }
-    __syncthreads();  // previous pass finished reading P / warp_tot
+    __syncthreads();  // previous pass finished reading P
     if (lane == 31) warp_tot[wid] = incl;
     __syncthreads();
-    long long woff = 0;
+    uint32_t woff = 0;
     for (int k = 0; k < wid; ++k) woff += warp_tot[k];
-    const long long excl = woff + incl - run;
+    const uint32_t excl = woff + incl - run;
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       if (e < E) P[1 + tid * E + e] = excl + vals[e];
     __syncthreads();
 
-    // ---- boxcars, block maxima, candidates
+    // ---- boxcars: block maxima against the integer bounds; exact path only where needed
     for (int e = 0; e < kSpsSeg / kSpsThreads; ++e) {
       const long long j = seg0 + e * kSpsThreads + tid;  // window sample
       const int u = H + e * kSpsThreads + tid;           // its entry in P (before the +1)
-      const bool leader = (tid & (B - 1)) == 0;
-      int32_t bestB[kMaxWidths];
-      int32_t bestJ[kMaxWidths];
-      float best32 = -INFINITY;
-      bool any = false;
+      const uint32_t pj = P[1 + u];
+      bool maybe = false;
 #pragma unroll
       for (int k = 0; k < kMaxWidths; ++k) {
         if (k < a.nw) {
           const int w = a.wd[k];
           const bool valid = (j < n) && (j >= w - 1);
-          unsigned long long key = 0;
-          if (valid) {
-            const long long bw = P[1 + u] - P[1 + u - w];
-            key = ((unsigned long long)bw << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)(tid & (B - 1)));
-          }
-          for (int off = B >> 1; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
-            key = o > key ? o : key;
-          }
-          bestB[k] = -1;
-          bestJ[k] = 0;
-          if (key != 0) {
-            bestB[k] = (int32_t)(key >> 32);
-            bestJ[k] = (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
-            const long long num = n * (long long)bestB[k] - (long long)w * s1;
-            best32 = fmaxf(best32, (float)num * inv32[k]);
-            any = true;
-          }
+          const uint32_t bw = valid ? pj - P[1 + u - w] : 0u;
+          const uint32_t mx = block_max(bw, B);
+          maybe |= (long long)mx >= bthr[k];
         }
       }
-      if (leader && any && best32 >= thr - margin) {
-        // exact decision in FP64, in the oracle's evaluation order
-        double bs = 0.0;
-        long long bj = 0;
-        int bw = 0;
-        bool have = false;
-        const long long jb = j;  // block start (leader has offset 0 in its block)
+      if (!__any_sync(0xffffffffu, maybe)) continue;
+      // exact: per width the block's largest boxcar (earliest sample), then the FP64 SNRs in
+      // the oracle's evaluation order; the block leader decides and emits
+      const bool leader = (tid & (B - 1)) == 0;
+      double bs = 0.0;
+      long long bj = 0;
+      int bwid = 0;
+      bool have = false;
 #pragma unroll
-        for (int k = 0; k < kMaxWidths; ++k) {
-          if (k < a.nw && bestB[k] >= 0) {
-            const int w = a.wd[k];
-            const long long num = n * (long long)bestB[k] - (long long)w * s1;
+      for (int k = 0; k < kMaxWidths; ++k) {
+        if (k < a.nw) {
+          const int w = a.wd[k];
+          const bool valid = (j < n) && (j >= w - 1);
+          const uint32_t bw = valid ? pj - P[1 + u - w] : 0u;
+          int off;
+          const int best = block_argmax(bw, valid, B, lane, off);
+          if (leader && best >= 0) {
+            const long long num = n * (long long)best - (long long)w * s1;
             const double snr = (double)num / den[k];
-            const long long jk = jb + bestJ[k];
+            const long long jk = j + off;  // the leader holds the block's first sample
             if (!have || snr > bs || (snr == bs && jk < bj)) {
               have = true;
               bs = snr;
               bj = jk;
-              bw = w;
+              bwid = w;
             }
           }
         }
-        if (have && bs >= (double)thr) {
-          const unsigned long long idx = atomicAdd(a.count, 1ull);
-          if ((long long)idx < a.cap) {
-            dd_cand_t c;
-            c.trial = i;
-            c.range = a.range;
-            c.t_start = (a.J0 + bj - bw + 1) * (long long)a.d;
-            c.width = bw * a.d;
-            c.pad = 0;
-            c.snr = bs;
-            a.cands[idx] = c;
-          }
+      }
+      if (leader && have && bs >= thr) {
+        const unsigned long long idx = atomicAdd(a.count, 1ull);
+        if ((long long)idx < a.cap) {
+          dd_cand_t c;
+          c.trial = i;
+          c.range = a.range;
+          c.t_start = (a.J0 + bj - bwid + 1) * (long long)a.d;
+          c.width = bwid * a.d;
+          c.pad = 0;
+          c.snr = bs;
+          a.cands[idx] = c;
         }
       }
     }
@@ -436,7 +452,7 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
 
 cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st) {
   if (a.n <= 0 || a.n_trials <= 0 || a.nw <= 0) return cudaSuccess;
-  const size_t smem = sizeof(long long) * (size_t)(1 + a.hist + kSpsSeg);
+  const size_t smem = sizeof(uint32_t) * (size_t)(1 + a.hist + kSpsSeg);
   k_sps<<<a.n_trials, kSpsThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
