@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         print("\n".join(errs))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-                           "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
+                           "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-Xlinker", "-z,defs"])
     os.replace(tmp, LIB_PATH)
     for o in objs:
         os.remove(o)

@@ -94,6 +94,7 @@ struct RangeKernel {
   int row_slot = 0;
   int zcap = 0;
   size_t smem = 0;
+  uint8_t* d_tabs = nullptr;  // device copy of the delay-class tables
 };
 
 struct dd_plan_s {
@@ -157,6 +158,7 @@ void free_plan(dd_plan_s* p) {
   }
   for (auto e : p->tev) cudaEventDestroy(e);
   if (p->tref) cudaEventDestroy(p->tref);
+  for (auto& k : p->rk) cudaFree(k.d_tabs);
   cudaFree(p->d_shifts);
   cudaFree(p->hist);
   cudaFreeHost(p->h_cands);
@@ -229,69 +231,6 @@ int timing_end(dd_plan_s* p, cudaStream_t st, int64_t slot) {
   if (slot < 0) return DD_OK;
   DD_CK(cudaEventRecord(p->tev[2 * slot + 1], st));
   return DD_OK;
-}
-
-// Size the tiled kernel for one range from its delay table [ntr][C4]: the largest delay spread
-// of a tile's trials in one channel (staged row length), and the largest number of pattern
-// words one stage of 4-channel groups needs (found exactly as the kernel finds them).
-RangeKernel plan_range_kernel(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
-  RangeKernel k;
-  const int D = ddk::tiled_trials_per_tile(), NG = ddk::tiled_groups_per_stage();
-  int64_t spread = 0, relmax = 0, zcap = 0;
-  for (int t0 = 0; t0 < ntr; t0 += D) {
-    const int n = std::min(D, ntr - t0);
-    for (int c = 0; c < c4; ++c) {
-      for (int i = 1; i < n; ++i)
-        if (tab[(int64_t)(t0 + i) * c4 + c] < tab[(int64_t)(t0 + i - 1) * c4 + c]) return k;
-      spread = std::max<int64_t>(spread, tab[(int64_t)(t0 + n - 1) * c4 + c] -
-                                             tab[(int64_t)t0 * c4 + c]);
-    }
-    for (int g0 = 0; g0 < c4 / 4; g0 += NG) {
-      int64_t stage = 0;
-      for (int g = g0; g < std::min(g0 + NG, c4 / 4); ++g) {
-        uint64_t key[256];
-        int bmin[256], bmax[256];
-        int np = 0;
-        for (int i = 0; i < n; ++i) {
-          const int32_t* s = tab + (int64_t)(t0 + i) * c4 + 4 * g;
-          const int b = std::min(std::min(s[0], s[1]), std::min(s[2], s[3]));
-          uint64_t kk = 0;
-          for (int q = 0; q < 4; ++q) {
-            relmax = std::max<int64_t>(relmax, s[q] - b);
-            kk |= (uint64_t)(uint32_t)(s[q] - b) << (16 * q);
-          }
-          int p = 0;
-          while (p < np && key[p] != kk) ++p;
-          if (p == np) {
-            key[np] = kk;
-            bmin[np] = bmax[np] = b;
-            ++np;
-          } else {
-            bmin[p] = std::min(bmin[p], b);
-            bmax[p] = std::max(bmax[p], b);
-          }
-        }
-        int items = 0;
-        for (int p = 0; p < np; ++p) {
-          const int zl = (tt + bmax[p] - bmin[p] + 3) & ~3;
-          stage += zl;
-          items += (zl / (u16 ? 2 : 4) + 31) / 32;
-        }
-        if (items > 128 || np > 255) return k;  // the kernel's per-group item table
-      }
-      zcap = std::max(zcap, stage);
-    }
-  }
-  if (relmax >= 65536 || spread > 65536) return k;
-  const int A = u16 ? 8 : 16;
-  k.tt = tt;
-  // staged row: up to A-1 elements of alignment in front, 16-byte rounding behind, and 16
-  // elements the word-wise pattern build may read past the last word it uses
-  k.row_slot = (int)round_up(tt + spread + 2 * A + 16, A);
-  k.zcap = (int)round_up(std::max<int64_t>(zcap, 1), 4);
-  k.smem = ddk::tiled_smem_bytes(u16, k.row_slot, k.zcap);
-  k.tiled = k.smem <= 200 * 1024;
-  return k;
 }
 
 }  // namespace
@@ -443,18 +382,29 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     if (!(o.flags & DD_FLAG_NAIVE)) {
       for (int r = 0; r < nranges; ++r) {
         const bool u16 = ranges[r].decimation > 1;
-        for (int tt : {ddk::tiled_tile_samples(u16, 0), ddk::tiled_tile_samples(u16, 1)}) {
-          RangeKernel k = plan_range_kernel(&full[(size_t)p->row0[r] * p->C4], ranges[r].n_trials,
-                                            p->C4, u16, tt);
-          if (k.tiled) {
-            cudaError_t e2 = ddk::prepare_tiled(u16, tt, k.smem);
-            if (e2 != cudaSuccess) {
-              free_plan(p);
-              return fail(DD_ERR_CUDA, "tiled kernel set-up: %s", cudaGetErrorString(e2));
-            }
-            p->rk[r] = k;
-            break;
+        for (int choice = 0; choice < 2; ++choice) {
+          const int tt = ddk::tiled_tile_samples(u16, choice);
+          ddk::TiledPlan tp = ddk::tiled_plan(&full[(size_t)p->row0[r] * p->C4],
+                                              ranges[r].n_trials, p->C4, u16, tt);
+          if (!tp.ok) continue;
+          RangeKernel& k = p->rk[r];
+          if (dalloc(&k.d_tabs, tp.tab_bytes, "delay-class tables")) {
+            free_plan(p);
+            return DD_ERR_NOMEM;
           }
+          cudaError_t e2 = cudaMemcpy(k.d_tabs, tp.tabs.data(), tp.tab_bytes,
+                                      cudaMemcpyHostToDevice);
+          if (e2 == cudaSuccess) e2 = ddk::prepare_tiled(u16, tt, tp.smem);
+          if (e2 != cudaSuccess) {
+            free_plan(p);
+            return fail(DD_ERR_CUDA, "tiled kernel set-up: %s", cudaGetErrorString(e2));
+          }
+          k.tiled = true;
+          k.tt = tt;
+          k.row_slot = tp.row_slot;
+          k.zcap = tp.zcap;
+          k.smem = tp.smem;
+          break;
         }
       }
     }
@@ -608,6 +558,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       A.c4 = p->C4;
       A.row_slot = K.row_slot;
       A.zcap = K.zcap;
+      A.tabs = K.d_tabs;
       A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
       DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, st));
       p->launches += 1;

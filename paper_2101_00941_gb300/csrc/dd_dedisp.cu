@@ -4,23 +4,25 @@
 // One CTA (16 warps) owns a tile of kTileTrials consecutive DM trials x TT output samples of one
 // range and walks the channels in stages of kNG groups of four channels.
 //
-//   * TMA (cp.async.bulk) stages the 16 channel rows of a stage into shared memory, kNStage
-//     stages ahead; completion is tracked by mbarriers with bounded waits.
-//   * For each 4-channel group the tile's trials fall into a few classes by the relative delays
-//     (r0, r1, r2, r3) of the four channels (found with __match_any_sync). A class shares one
-//     "pattern word" sequence
+//   * Delay classes. For a 4-channel group the tile's trials fall into a few classes by the
+//     relative delays (r0, r1, r2, r3) of the four channels. A class shares one "pattern word"
+//     sequence
 //        Z_p[u] = x[c0][a + u + r0] | x[c1][a + u + r1] << 8 | x[c2][..] << 16 | x[c3][..] << 24
-//     that each of its trials reads at its own base offset b.
+//     that each of its trials reads at its own base offset. The classes depend on the delay
+//     table only, so the plan computes them once (tiled_plan, below) as one fixed-size table per
+//     (trial tile, stage); the kernel never searches for them.
+//   * TMA (cp.async.bulk) brings each stage's 16 channel rows and its class table into shared
+//     memory kNStage stages ahead; completion is tracked by mbarriers with bounded waits.
 //   * The main loop adds one pattern word per (trial, sample): DP4A for uint8 data, two DP2A
 //     for uint16 (decimated) data -- one shared-memory load per four channel-adds.
 //
 // Software pipeline, one __syncthreads per stage s:
-//     issue TMA for stage s+kNStage-1 | find classes of stage s+2 | build words of stage s+1 |
-//     accumulate stage s
-// The words are built four (uint8) or two (uint16) at a time from aligned 32-bit loads,
-// funnel shifts and a byte transpose. Exact moments (S1, 128-bit S2) of every series are added
-// in the epilogue with integer atomics, so the search needs no second statistics pass.
-#include <climits>
+//     TMA for stage s+kNStage-1 | build the words of stage s+1 | accumulate stage s
+// Words are built four (uint8) or two (uint16) at a time from aligned 32-bit loads, funnel
+// shifts and a byte transpose. Exact moments (S1, 128-bit S2) of every series are added in the
+// epilogue with integer atomics, so the search needs no second statistics pass.
+#include <algorithm>
+#include <cstring>
 
 #include "dd_internal.h"
 
@@ -34,29 +36,35 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kTPW = kTileTrials / kWarps;  // trials per warp
 constexpr int kNG = 4;                      // 4-channel groups per stage
 constexpr int kRows = 4 * kNG;              // channel rows per stage
-constexpr int kNStage = 4;                  // raw staging buffers
-constexpr int kNTab = 3;                    // class tables in flight (stages s, s+1, s+2)
-constexpr int kMaxItems = 128;              // build items (32 units of one class) per group
+constexpr int kNStage = 4;                  // staging buffers (rows + class table)
+constexpr int kMaxCls = 8;                  // classes per group
+constexpr int kMaxItems = 32;               // build items (32 units of one class) per group
 
-struct PatEntry {
-  int32_t col[4];  // staged element of each channel row for word u = 0
-  int32_t zoff;    // first word of the class within its group (multiple of 4)
-  int32_t zlen;    // words of the class (multiple of 4)
+// One delay class: its channels' first staged sample relative to the tile's first trial
+// (rel), and its words in the stage's pattern-word region.
+struct ClsEntry {
+  int16_t rel[4];
+  int16_t zoff;  // first word (multiple of 4)
+  int16_t zlen;  // words (multiple of 4)
+  int32_t pad;
+};
+
+struct GroupTab {
+  int16_t zstart[kTileTrials];  // stage word offset of each trial's sequence (0 for no trial)
+  ClsEntry cls[kMaxCls];
+  uint16_t item[kMaxItems];     // class << 8 | segment of 32 units
+  int32_t ncls, nitem, pad0, pad1;
 };
 
 struct StageTab {
-  int32_t zstart[kNG][kTileTrials];  // word offset of each trial's sequence within its group
-  PatEntry pat[kNG][kTileTrials];
-  uint16_t item[kNG][kMaxItems];     // build items: class << 8 | segment of 32 units
-  int32_t gtot[kNG];                 // words of each group
-  int32_t npat[kNG];
-  int32_t nitem[kNG];
+  GroupTab g[kNG];
 };
+static_assert(sizeof(StageTab) % 16 == 0, "class tables are copied in 16-byte units");
 
 __host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 struct SmemLayout {
-  size_t raw, z, tab, mbar, total;
+  size_t raw, z, tab, phase, mbar, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot, int zcap) {
@@ -67,7 +75,9 @@ __host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot,
   L.z = off;
   off = align16(off + (size_t)2 * zcap * zes);
   L.tab = off;
-  off = align16(off + sizeof(StageTab) * kNTab);
+  off = align16(off + sizeof(StageTab) * kNStage);
+  L.phase = off;
+  off = align16(off + sizeof(int32_t) * kNStage * kRows);
   L.mbar = off;
   off = align16(off + sizeof(unsigned long long) * kNStage);
   L.total = off;
@@ -126,35 +136,30 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Delays bounding one stage's channel rows for this tile: lane k < kRows loads the first and the
-// last trial's delay of channel stage*kRows + k (delays are non-decreasing in the trial index).
-__device__ __forceinline__ void stage_bounds(const TiledArgs& a, int stage, int lane, int trial0,
-                                             int ntr, int& smin, int& smax) {
-  const int c = stage * kRows + lane;
-  smin = smax = 0;
-  if (lane < kRows && c < a.c4) {
-    smin = __ldg(a.shifts + (int64_t)trial0 * a.c4 + c);
-    smax = __ldg(a.shifts + (int64_t)(trial0 + ntr - 1) * a.c4 + c);
-  }
-}
-
-// Warp-cooperative issue of one stage: lane k copies channel row k with one bulk (TMA) copy of
-// whole 16-byte units covering [m0 + j0 + smin, m0 + j0 + smax + TT); lane 0 first arms the
-// stage's mbarrier with the total byte count.
+// Warp-cooperative issue of one stage (one warp): lane k < kRows copies channel row k --
+// whole 16-byte units covering [m0 + j0 + s_first, m0 + j0 + s_last + TT) -- and records the
+// sample's phase within the first unit; lane kRows copies the stage's class table. Lane 0 first
+// arms the stage's mbarrier with the total byte count.
 template <typename T, int TT>
-__device__ void issue_stage(const TiledArgs& a, int stage, T* raw_buf, unsigned long long* bar,
-                            int64_t j0, int lane, int smin, int smax) {
+__device__ void issue_stage(const TiledArgs& a, int stage, int nstages, T* raw_buf,
+                            StageTab* tab_buf, int32_t* phase_buf, unsigned long long* bar,
+                            int trial0, int ntr, int64_t j0, int lane) {
   constexpr int A = 16 / (int)sizeof(T);  // elements per 16 bytes
   const int c = stage * kRows + lane;
   const bool mine = lane < kRows && c < a.c4;
   int64_t a0 = 0;
   uint32_t nb = 0;
   if (mine) {
+    const int32_t smin = __ldg(a.shifts + (int64_t)trial0 * a.c4 + c);
+    const int32_t smax = __ldg(a.shifts + (int64_t)(trial0 + ntr - 1) * a.c4 + c);
     const int64_t start = a.m0 + j0 + smin;
     a0 = start & ~(int64_t)(A - 1);
     const int64_t end = a.m0 + j0 + smax + TT;
     nb = (uint32_t)(((end - a0) * (int64_t)sizeof(T) + 15) & ~int64_t(15));
+    phase_buf[lane] = (int32_t)(start - a0);
   }
+  if (lane == kRows) nb = (uint32_t)sizeof(StageTab);
+  __syncwarp();  // the phases written above are released by lane 0's arrive below
   uint32_t total = nb;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) total += __shfl_xor_sync(0xffffffffu, total, off);
@@ -166,96 +171,9 @@ __device__ void issue_stage(const TiledArgs& a, int stage, T* raw_buf, unsigned 
   if (mine)
     bulk_g2s(raw_buf + (size_t)lane * a.row_slot,
              static_cast<const T*>(a.xd) + (int64_t)c * a.xd_stride + a0, nb, bar);
-}
-
-// Classes of one 4-channel group (one warp; lane l holds trials l and l + 32 of the tile).
-// `s4[h]` are the delays of the group's four channels for trial l + 32h, `f4` those of the
-// tile's first trial. Classes are peeled off one at a time (a handful per group), each loop
-// iteration a few warp-wide votes and reductions.
-template <typename T, int TT>
-__device__ __forceinline__ void find_classes(const TiledArgs& a, StageTab& tb, int g, int lane,
-                                             int ntr, int64_t j0, const int4 (&s4)[2], int4 f4) {
-  constexpr int A = 16 / (int)sizeof(T);
-  unsigned long long key[2];
-  int b[2];
-  uint32_t rem[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    b[h] = min(min(s4[h].x, s4[h].y), min(s4[h].z, s4[h].w));
-    key[h] = (unsigned long long)(uint32_t)(s4[h].x - b[h]) |
-             ((unsigned long long)(uint32_t)(s4[h].y - b[h]) << 16) |
-             ((unsigned long long)(uint32_t)(s4[h].z - b[h]) << 32) |
-             ((unsigned long long)(uint32_t)(s4[h].w - b[h]) << 48);
-    rem[h] = __ballot_sync(0xffffffffu, lane + 32 * h < ntr);
-  }
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-    if (lane + 32 * h >= ntr) tb.zstart[g][lane + 32 * h] = 0;  // absent trial: a valid dummy
-  constexpr int U = 16 / (int)sizeof(T) / 4;  // pattern words per build unit: 4 (u8), 2 (u16)
-  int npat = 0, zoff = 0, nitem = 0;
-  while (rem[0] | rem[1]) {
-    const int hl = rem[0] ? 0 : 1;
-    const int L = __ffs(hl ? rem[1] : rem[0]) - 1;
-    const unsigned long long kk = __shfl_sync(0xffffffffu, hl ? key[1] : key[0], L);
-    bool in[2];
-    int lo = INT_MAX, hi = INT_MIN;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      in[h] = ((rem[h] >> lane) & 1u) && key[h] == kk;
-      rem[h] &= ~__ballot_sync(0xffffffffu, in[h]);
-      if (in[h]) {
-        lo = min(lo, b[h]);
-        hi = max(hi, b[h]);
-      }
-    }
-    const int bmin = __reduce_min_sync(0xffffffffu, lo);
-    const int bmax = __reduce_max_sync(0xffffffffu, hi);
-    const int zlen = (TT + bmax - bmin + 3) & ~3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-      if (in[h]) tb.zstart[g][lane + 32 * h] = zoff + (b[h] - bmin);
-    if (lane == 0) {
-      const int64_t base = a.m0 + j0 + bmin;
-      PatEntry e;
-      e.col[0] = (int32_t)(base + (int)(kk & 0xFFFF) - ((a.m0 + j0 + f4.x) & ~(int64_t)(A - 1)));
-      e.col[1] = (int32_t)(base + (int)((kk >> 16) & 0xFFFF) -
-                           ((a.m0 + j0 + f4.y) & ~(int64_t)(A - 1)));
-      e.col[2] = (int32_t)(base + (int)((kk >> 32) & 0xFFFF) -
-                           ((a.m0 + j0 + f4.z) & ~(int64_t)(A - 1)));
-      e.col[3] = (int32_t)(base + (int)(kk >> 48) - ((a.m0 + j0 + f4.w) & ~(int64_t)(A - 1)));
-      e.zoff = zoff;
-      e.zlen = zlen;
-      tb.pat[g][npat] = e;
-    }
-    const int nseg = (zlen / U + 31) >> 5;
-    for (int q = lane; q < nseg; q += 32)
-      if (nitem + q < kMaxItems) tb.item[g][nitem + q] = (uint16_t)((npat << 8) | q);
-    nitem += nseg;
-    zoff += zlen;
-    ++npat;
-  }
-  if (lane == 0) {
-    tb.gtot[g] = zoff;
-    tb.npat[g] = npat;
-    tb.nitem[g] = nitem;
-  }
-}
-
-// Delays of one group's four channels for trials lane and lane + 32 of the tile.
-__device__ __forceinline__ void load_group_delays(const TiledArgs& a, int trial0, int ntr,
-                                                  int gabs, int lane, int4 (&s4)[2]) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    s4[h] = make_int4(0, 0, 0, 0);
-    if (lane + 32 * h < ntr)
-      s4[h] = __ldg(reinterpret_cast<const int4*>(a.shifts + (int64_t)(trial0 + lane + 32 * h) *
-                                                                 a.c4 + 4 * gabs));
-  }
-}
-
-__device__ __forceinline__ int4 first_trial(int4 s4) {
-  return make_int4(__shfl_sync(0xffffffffu, s4.x, 0), __shfl_sync(0xffffffffu, s4.y, 0),
-                   __shfl_sync(0xffffffffu, s4.z, 0), __shfl_sync(0xffffffffu, s4.w, 0));
+  if (lane == kRows)
+    bulk_g2s(tab_buf, a.tabs + ((size_t)blockIdx.x * nstages + stage) * sizeof(StageTab),
+             (uint32_t)sizeof(StageTab), bar);
 }
 
 template <typename T>
@@ -273,13 +191,13 @@ struct Word<uint8_t> {
     uint32_t sh[4];         // bit phase of that sample in the word
   };
   static __device__ __forceinline__ Item item(const uint8_t* rawb, int row_slot, int g,
-                                              const PatEntry& e) {
+                                              const int (&col)[4]) {
     Item it;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       it.rp[k] = reinterpret_cast<const uint32_t*>(rawb + (size_t)(4 * g + k) * row_slot) +
-                 (e.col[k] >> 2);
-      it.sh[k] = (uint32_t)(e.col[k] & 3) * 8u;
+                 (col[k] >> 2);
+      it.sh[k] = (uint32_t)(col[k] & 3) * 8u;
     }
     return it;
   }
@@ -313,13 +231,13 @@ struct Word<uint16_t> {
     uint32_t sh[4];
   };
   static __device__ __forceinline__ Item item(const uint16_t* rawb, int row_slot, int g,
-                                              const PatEntry& e) {
+                                              const int (&col)[4]) {
     Item it;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       it.rp[k] = reinterpret_cast<const uint32_t*>(rawb + (size_t)(4 * g + k) * row_slot) +
-                 (e.col[k] >> 1);
-      it.sh[k] = (uint32_t)(e.col[k] & 1) * 16u;
+                 (col[k] >> 1);
+      it.sh[k] = (uint32_t)(col[k] & 1) * 16u;
     }
     return it;
   }
@@ -340,42 +258,30 @@ struct Word<uint16_t> {
   }
 };
 
-// Build every pattern word of one stage. The work is cut into items of 32 units of one class
-// (listed by the class search); warps w0 .. kWarps-1 take the items round-robin and each lane
-// builds one unit of an item.
+// Build every pattern word of one stage. The plan cut the work into items of 32 units of one
+// class; warp w takes items w, w + kWarps, ... and each lane builds one unit of an item.
 template <typename T>
 __device__ __forceinline__ void build_stage(const StageTab& tb, int ng, const T* rawb,
-                                            int row_slot, typename Word<T>::Z* Zs, int warp,
-                                            int lane, int w0) {
+                                            const int32_t* phase, int row_slot,
+                                            typename Word<T>::Z* Zs, int warp, int lane) {
   constexpr int U = Word<T>::kUnit;
-  if (warp < w0) return;
-  int ibeg[kNG + 1], wbeg[kNG];
-  ibeg[0] = 0;
-  int words = 0;
+  const int n0 = tb.g[0].nitem;
+  const int n1 = n0 + (ng > 1 ? tb.g[1].nitem : 0);
+  const int n2 = n1 + (ng > 2 ? tb.g[2].nitem : 0);
+  const int n3 = n2 + (ng > 3 ? tb.g[3].nitem : 0);
+  for (int k = warp; k < n3; k += kWarps) {
+    const int gi = (k >= n0) + (k >= n1) + (k >= n2);
+    const int kb = gi == 0 ? 0 : gi == 1 ? n0 : gi == 2 ? n1 : n2;
+    const GroupTab& gt = tb.g[gi];
+    const uint32_t itw = gt.item[k - kb];
+    const ClsEntry e = gt.cls[itw >> 8];
+    int col[4];
 #pragma unroll
-  for (int g = 0; g < kNG; ++g) {
-    wbeg[g] = words;
-    ibeg[g + 1] = ibeg[g] + (g < ng ? tb.nitem[g] : 0);
-    words += (g < ng ? tb.gtot[g] : 0);
-  }
-  for (int k = warp - w0; k < ibeg[kNG]; k += kWarps - w0) {
-    const int gi = (k >= ibeg[1]) + (k >= ibeg[2]) + (k >= ibeg[3]);
-    const int kb = gi == 0 ? ibeg[0] : gi == 1 ? ibeg[1] : gi == 2 ? ibeg[2] : ibeg[3];
-    const int zb = gi == 0 ? wbeg[0] : gi == 1 ? wbeg[1] : gi == 2 ? wbeg[2] : wbeg[3];
-    const uint32_t itw = tb.item[gi][k - kb];
-    const PatEntry& e = tb.pat[gi][itw >> 8];
-    const typename Word<T>::Item it = Word<T>::item(rawb, row_slot, gi, e);
+    for (int q = 0; q < 4; ++q) col[q] = e.rel[q] + phase[4 * gi + q];
+    const typename Word<T>::Item it = Word<T>::item(rawb, row_slot, gi, col);
     const int m = (int)(itw & 255) * 32 + lane;
-    if (m * U < e.zlen) Word<T>::build(it, m, Zs + zb + e.zoff);
+    if (m * U < e.zlen) Word<T>::build(it, m, Zs + e.zoff);
   }
-}
-
-__device__ __forceinline__ int stage_words(const StageTab& tb, int ng) {
-  int tot = 0;
-#pragma unroll
-  for (int g = 0; g < kNG; ++g)
-    if (g < ng) tot += tb.gtot[g];
-  return tot;
 }
 
 template <typename T, int TT>
@@ -387,6 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
   T* raw = reinterpret_cast<T*>(smem + SL.raw);
   ZT* Zbuf = reinterpret_cast<ZT*>(smem + SL.z);
   StageTab* tab = reinterpret_cast<StageTab*>(smem + SL.tab);
+  int32_t* phase = reinterpret_cast<int32_t*>(smem + SL.phase);
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + SL.mbar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -406,29 +313,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
   // stages whose copies have been issued: kNStage in the prologue, then one per iteration s >= 1
   // (the same count in every thread)
   int issued = min(kNStage, nstages);
-  if (warp == 0) {
-    for (int s = 0; s < kNStage && s < nstages; ++s) {
-      int smin, smax;
-      stage_bounds(a, s, lane, trial0, ntr, smin, smax);
-      issue_stage<T, TT>(a, s, raw + (size_t)s * stage_elems, &mbar[s], j0, lane, smin, smax);
-    }
+  if (warp == kWarps - 1) {
+    for (int s = 0; s < kNStage && s < nstages; ++s)
+      issue_stage<T, TT>(a, s, nstages, raw + (size_t)s * stage_elems, &tab[s],
+                         phase + s * kRows, &mbar[s], trial0, ntr, j0, lane);
   }
-  // classes of stages 0 and 1 (warps 0..kNG-1 and kNG..2kNG-1)
-  {
-    const int st = warp / kNG, g = warp % kNG;
-    if (st < 2 && st < nstages && st * kNG + g < ngroups) {
-      int4 s4[2];
-      load_group_delays(a, trial0, ntr, st * kNG + g, lane, s4);
-      find_classes<T, TT>(a, tab[st], g, lane, ntr, j0, s4, first_trial(s4[0]));
-    }
-  }
-  // delays of the group this warp classifies next (stage 2), loaded one stage ahead
-  int4 pre[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
-  if (warp < kNG && 2 < nstages && 2 * kNG + warp < ngroups)
-    load_group_delays(a, trial0, ntr, 2 * kNG + warp, lane, pre);
-  __syncthreads();
-  bool ok0 = stage_words(tab[0], min(kNG, ngroups)) <= a.zcap && mbar_wait_bounded(&mbar[0], 0);
-  if (ok0) build_stage<T>(tab[0], min(kNG, ngroups), raw, a.row_slot, Zbuf, warp, lane, 0);
+  bool ok0 = mbar_wait_bounded(&mbar[0], 0);
+  if (ok0) build_stage<T>(tab[0], min(kNG, ngroups), raw, phase, a.row_slot, Zbuf, warp, lane);
   bool aborted = __syncthreads_or(!ok0);
   int s_abort = 0;  // first stage whose copies may still be in flight
 
@@ -440,52 +331,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
 
   for (int s = 0; s < nstages && !aborted; ++s) {
     const int ng = min(kNG, ngroups - s * kNG);
-    // (1) TMA for stage s + kNStage - 1 into the buffer stage s - 1 used (built during s - 2)
+    // (1) TMA for stage s + kNStage - 1 into the buffers stage s - 1 used (its words were built
+    //     during stage s - 2 and its table last read by the accumulation of stage s - 1)
     if (s >= 1 && s + kNStage - 1 < nstages) {
       const int s2 = s + kNStage - 1;
-      if (warp == kWarps - 1) {
-        int smin, smax;
-        stage_bounds(a, s2, lane, trial0, ntr, smin, smax);
-        issue_stage<T, TT>(a, s2, raw + (size_t)(s2 % kNStage) * stage_elems,
-                           &mbar[s2 % kNStage], j0, lane, smin, smax);
-      }
+      const int b2 = s2 % kNStage;
+      if (warp == kWarps - 1)
+        issue_stage<T, TT>(a, s2, nstages, raw + (size_t)b2 * stage_elems, &tab[b2],
+                           phase + b2 * kRows, &mbar[b2], trial0, ntr, j0, lane);
       issued = s2 + 1;
     }
-    // (2) classes of stage s + 2
-    if (warp < kNG && s + 2 < nstages && (s + 2) * kNG + warp < ngroups) {
-      find_classes<T, TT>(a, tab[(s + 2) % kNTab], warp, lane, ntr, j0, pre, first_trial(pre[0]));
-      pre[0] = pre[1] = make_int4(0, 0, 0, 0);
-      if (s + 3 < nstages && (s + 3) * kNG + warp < ngroups)
-        load_group_delays(a, trial0, ntr, (s + 3) * kNG + warp, lane, pre);
-    }
-    // (3) pattern words of stage s + 1
+    // (2) pattern words of stage s + 1
     bool ok = true;
     if (s + 1 < nstages) {
-      const StageTab& tn = tab[(s + 1) % kNTab];
-      const int ng1 = min(kNG, ngroups - (s + 1) * kNG);
-      ok = stage_words(tn, ng1) <= a.zcap &&
-           mbar_wait_bounded(&mbar[(s + 1) % kNStage], (uint32_t)(((s + 1) / kNStage) & 1));
+      const int b1 = (s + 1) % kNStage;
+      ok = mbar_wait_bounded(&mbar[b1], (uint32_t)(((s + 1) / kNStage) & 1));
       if (ok)
-        build_stage<T>(tn, ng1, raw + (size_t)((s + 1) % kNStage) * stage_elems, a.row_slot,
-                       Zbuf + (size_t)((s + 1) & 1) * a.zcap, warp, lane,
-                       s + 2 < nstages ? kNG : 0);  // classifying warps sit out
+        build_stage<T>(tab[b1], min(kNG, ngroups - (s + 1) * kNG), raw + (size_t)b1 * stage_elems,
+                       phase + b1 * kRows, a.row_slot, Zbuf + (size_t)((s + 1) & 1) * a.zcap,
+                       warp, lane);
     }
-    // (4) accumulate stage s
+    // (3) accumulate stage s
     {
-      const StageTab& tc = tab[s % kNTab];
+      const StageTab& tc = tab[s % kNStage];
       const ZT* Zs = Zbuf + (size_t)(s & 1) * a.zcap + lane;
-      int gb = 0;
 #pragma unroll
       for (int g = 0; g < kNG; ++g) {
         if (g < ng) {  // uniform; only the last stage may hold fewer groups
           const ZT* zp[kTPW];
 #pragma unroll
-          for (int q = 0; q < kTPW; ++q) zp[q] = Zs + gb + tc.zstart[g][warp + kWarps * q];
+          for (int q = 0; q < kTPW; ++q) zp[q] = Zs + tc.g[g].zstart[warp + kWarps * q];
 #pragma unroll
           for (int k = 0; k < KT; ++k)
 #pragma unroll
             for (int q = 0; q < kTPW; ++q) acc[q][k] = Word<T>::dot(zp[q][32 * k], acc[q][k]);
-          gb += tc.gtot[g];
         }
       }
     }
@@ -569,17 +448,108 @@ cudaError_t prepare_t(size_t smem) {
 
 }  // namespace
 
-int tiled_trials_per_tile() { return kTileTrials; }
-int tiled_groups_per_stage() { return kNG; }
-
-size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap) {
-  return smem_layout(is_u16 ? 2 : 1, is_u16 ? 8 : 4, row_slot, zcap).total;
-}
-
 int tiled_tile_samples(int is_u16, int choice) {
   // preferred time tile first, a smaller one when the first does not fit shared memory
   if (!is_u16) return choice == 0 ? 512 : 256;
   return choice == 0 ? 256 : 128;
+}
+
+// Host: delay classes of every (trial tile, stage) of one range, as the kernel reads them.
+// Classes are numbered in order of their first trial; a class's words start at a multiple of 4
+// within the stage, groups one after another.
+TiledPlan tiled_plan(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
+  TiledPlan P;
+  P.ok = false;
+  const int D = kTileTrials, NG = kNG, U = u16 ? 2 : 4;
+  const int ngroups = c4 / 4, nstages = (ngroups + NG - 1) / NG;
+  const int ntiles = (ntr + D - 1) / D;
+  int64_t spread = 0, zcap = 0;
+  std::vector<StageTab> out((size_t)ntiles * nstages);
+  for (int ti = 0; ti < ntiles; ++ti) {
+    const int t0 = ti * D, n = std::min(D, ntr - t0);
+    for (int c = 0; c < c4; ++c) {
+      for (int i = 1; i < n; ++i)
+        if (tab[(int64_t)(t0 + i) * c4 + c] < tab[(int64_t)(t0 + i - 1) * c4 + c]) return P;
+      spread = std::max<int64_t>(spread, tab[(int64_t)(t0 + n - 1) * c4 + c] -
+                                             tab[(int64_t)t0 * c4 + c]);
+    }
+    for (int s = 0; s < nstages; ++s) {
+      StageTab& st = out[(size_t)ti * nstages + s];
+      std::memset(&st, 0, sizeof st);
+      int words = 0;
+      for (int gl = 0; gl < NG && s * NG + gl < ngroups; ++gl) {
+        const int g = s * NG + gl;
+        GroupTab& gt = st.g[gl];
+        const int32_t* first = tab + (int64_t)t0 * c4 + 4 * g;
+        int b[kTileTrials], cls_of[kTileTrials];
+        uint64_t ckey[kTileTrials];
+        int cmin[kTileTrials], cmax[kTileTrials];
+        int ncls = 0;
+        for (int i = 0; i < n; ++i) {
+          const int32_t* sv = tab + (int64_t)(t0 + i) * c4 + 4 * g;
+          b[i] = std::min(std::min(sv[0], sv[1]), std::min(sv[2], sv[3]));
+          uint64_t kk = 0;
+          for (int q = 0; q < 4; ++q) {
+            const int64_t r = (int64_t)sv[q] - b[i];
+            if (r > 32767) return P;
+            kk |= (uint64_t)r << (16 * q);
+          }
+          int p = 0;
+          while (p < ncls && ckey[p] != kk) ++p;
+          if (p == ncls) {
+            ckey[ncls] = kk;
+            cmin[ncls] = cmax[ncls] = b[i];
+            ++ncls;
+          } else {
+            cmin[p] = std::min(cmin[p], b[i]);
+            cmax[p] = std::max(cmax[p], b[i]);
+          }
+          cls_of[i] = p;
+        }
+        if (ncls > kMaxCls) return P;
+        int nitem = 0;
+        int zoff[kTileTrials];
+        for (int p = 0; p < ncls; ++p) {
+          const int zlen = (tt + cmax[p] - cmin[p] + 3) & ~3;
+          zoff[p] = words;
+          ClsEntry& e = gt.cls[p];
+          for (int q = 0; q < 4; ++q) {
+            const int64_t rel = (int64_t)cmin[p] + (int64_t)((ckey[p] >> (16 * q)) & 0xFFFF) -
+                                first[q];
+            if (rel < 0 || rel > 32767) return P;
+            e.rel[q] = (int16_t)rel;
+          }
+          e.zoff = (int16_t)words;
+          e.zlen = (int16_t)zlen;
+          const int nseg = (zlen / U + 31) / 32;
+          for (int q = 0; q < nseg; ++q) {
+            if (nitem >= kMaxItems) return P;
+            gt.item[nitem++] = (uint16_t)((p << 8) | q);
+          }
+          words += zlen;
+          if (words > 32767) return P;
+        }
+        for (int i = 0; i < n; ++i)
+          gt.zstart[i] = (int16_t)(zoff[cls_of[i]] + b[i] - cmin[cls_of[i]]);
+        gt.ncls = ncls;
+        gt.nitem = nitem;
+      }
+      zcap = std::max<int64_t>(zcap, words);
+    }
+  }
+  if (spread > 65536) return P;
+  const int A = u16 ? 8 : 16;
+  P.tt = tt;
+  // staged row: up to A-1 elements of alignment in front, 16-byte rounding behind, and 16
+  // elements the word-wise build may read past the last word it uses
+  P.row_slot = (int)(((tt + spread + 2 * A + 16) + A - 1) / A * A);
+  P.zcap = (int)((std::max<int64_t>(zcap, 4) + 3) / 4 * 4);
+  P.smem = smem_layout(u16 ? 2 : 1, u16 ? 8 : 4, P.row_slot, P.zcap).total;
+  P.tab_bytes = out.size() * sizeof(StageTab);
+  P.tabs.resize(P.tab_bytes);
+  std::memcpy(P.tabs.data(), out.data(), P.tab_bytes);
+  P.ok = P.smem <= 200 * 1024;
+  return P;
 }
 
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem) {

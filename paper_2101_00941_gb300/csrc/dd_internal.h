@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "dd.h"
 
 namespace ddk {
@@ -79,13 +81,24 @@ struct TiledArgs {
   int32_t c4;
   int32_t row_slot;        // elements per staged channel row
   int32_t zcap;            // pattern words per stage
-  int32_t* err;            // bit 0: a bounded wait ran out; bit 1: pattern buffer too small
+  const uint8_t* tabs;     // delay-class tables of the range, one per (trial tile, stage)
+  int32_t* err;            // bit 0: a bounded wait ran out
 };
 
-int tiled_trials_per_tile();
+// Plan of the tiled kernel for one range (host): tile shape, shared-memory sizes and the
+// delay-class tables the kernel copies in per stage. ok = false: the range does not fit.
+struct TiledPlan {
+  bool ok = false;
+  int tt = 0;
+  int row_slot = 0;
+  int zcap = 0;
+  size_t smem = 0;
+  size_t tab_bytes = 0;
+  std::vector<uint8_t> tabs;
+};
+
 int tiled_tile_samples(int is_u16, int choice);
-int tiled_groups_per_stage();
-size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap);
+TiledPlan tiled_plan(const int32_t* shifts, int ntr, int c4, bool u16, int tt);
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st);
 
