@@ -38,7 +38,7 @@ constexpr int kNG = 4;                      // 4-channel groups per stage
 constexpr int kRows = 4 * kNG;              // channel rows per stage
 constexpr int kNStage = 4;                  // staging buffers (rows + class table)
 constexpr int kMaxCls = 8;                  // classes per group
-constexpr int kMaxItems = 32;               // build items (32 units of one class) per group
+constexpr int kMaxItems = 32;               // build items (64 units of one class) per group
 
 // One delay class: its channels' first staged sample relative to the tile's first trial
 // (rel), and its words in the stage's pattern-word region.
@@ -52,7 +52,7 @@ struct ClsEntry {
 struct GroupTab {
   int16_t zstart[kTileTrials];  // stage word offset of each trial's sequence (0 for no trial)
   ClsEntry cls[kMaxCls];
-  uint16_t item[kMaxItems];     // class << 8 | segment of 32 units
+  uint16_t item[kMaxItems];     // class << 8 | segment of 64 units
   int32_t ncls, nitem, pad0, pad1;
 };
 
@@ -201,11 +201,7 @@ struct Word<uint8_t> {
     }
     return it;
   }
-  // unit m = pattern words 4m .. 4m + 3
-  static __device__ __forceinline__ void build(const Item& it, int m, Z* dst) {
-    uint32_t v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __funnelshift_r(it.rp[k][m], it.rp[k][m + 1], it.sh[k]);
+  static __device__ __forceinline__ uint4 transpose(const uint32_t (&v)[4]) {
     // 4x4 byte transpose: word t gets byte t of every channel
     const uint32_t a0 = __byte_perm(v[0], v[1], 0x5140), a1 = __byte_perm(v[0], v[1], 0x7362);
     const uint32_t a2 = __byte_perm(v[2], v[3], 0x5140), a3 = __byte_perm(v[2], v[3], 0x7362);
@@ -214,7 +210,19 @@ struct Word<uint8_t> {
     o.y = __byte_perm(a0, a2, 0x7632);
     o.z = __byte_perm(a1, a3, 0x5410);
     o.w = __byte_perm(a1, a3, 0x7632);
-    reinterpret_cast<uint4*>(dst)[m] = o;
+    return o;
+  }
+  // units 2p and 2p + 1 = pattern words 8p .. 8p + 7 (three row words per channel)
+  static __device__ __forceinline__ void build2(const Item& it, int p, bool second, Z* dst) {
+    uint32_t v0[4], v1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t w0 = it.rp[k][2 * p], w1 = it.rp[k][2 * p + 1], w2 = it.rp[k][2 * p + 2];
+      v0[k] = __funnelshift_r(w0, w1, it.sh[k]);
+      v1[k] = __funnelshift_r(w1, w2, it.sh[k]);
+    }
+    reinterpret_cast<uint4*>(dst)[2 * p] = transpose(v0);
+    if (second) reinterpret_cast<uint4*>(dst)[2 * p + 1] = transpose(v1);
   }
   static __device__ __forceinline__ uint32_t dot(uint32_t z, uint32_t acc) {
     return __dp4a(z, 0x01010101u, acc);
@@ -241,25 +249,33 @@ struct Word<uint16_t> {
     }
     return it;
   }
-  // unit m = pattern words 2m, 2m + 1
-  static __device__ __forceinline__ void build(const Item& it, int m, Z* dst) {
-    uint32_t v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __funnelshift_r(it.rp[k][m], it.rp[k][m + 1], it.sh[k]);
+  static __device__ __forceinline__ uint4 pack(const uint32_t (&v)[4]) {
     uint4 o;
     o.x = __byte_perm(v[0], v[1], 0x5410);  // word 2m:   channels 0,1
     o.y = __byte_perm(v[2], v[3], 0x5410);  //            channels 2,3
     o.z = __byte_perm(v[0], v[1], 0x7632);  // word 2m+1: channels 0,1
     o.w = __byte_perm(v[2], v[3], 0x7632);  //            channels 2,3
-    reinterpret_cast<uint4*>(dst)[m] = o;
+    return o;
+  }
+  // units 2p and 2p + 1 = pattern words 4p .. 4p + 3 (three row words per channel)
+  static __device__ __forceinline__ void build2(const Item& it, int p, bool second, Z* dst) {
+    uint32_t v0[4], v1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t w0 = it.rp[k][2 * p], w1 = it.rp[k][2 * p + 1], w2 = it.rp[k][2 * p + 2];
+      v0[k] = __funnelshift_r(w0, w1, it.sh[k]);
+      v1[k] = __funnelshift_r(w1, w2, it.sh[k]);
+    }
+    reinterpret_cast<uint4*>(dst)[2 * p] = pack(v0);
+    if (second) reinterpret_cast<uint4*>(dst)[2 * p + 1] = pack(v1);
   }
   static __device__ __forceinline__ uint32_t dot(uint2 z, uint32_t acc) {
     return __dp2a_lo(z.y, 0x0101u, __dp2a_lo(z.x, 0x0101u, acc));
   }
 };
 
-// Build every pattern word of one stage. The plan cut the work into items of 32 units of one
-// class; warp w takes items w, w + kWarps, ... and each lane builds one unit of an item.
+// Build every pattern word of one stage. The plan cut the work into items of 64 units of one
+// class; warp w takes items w, w + kWarps, ... and each lane builds two adjacent units.
 template <typename T>
 __device__ __forceinline__ void build_stage(const StageTab& tb, int ng, const T* rawb,
                                             const int32_t* phase, int row_slot,
@@ -279,8 +295,8 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, int ng, const T*
 #pragma unroll
     for (int q = 0; q < 4; ++q) col[q] = e.rel[q] + phase[4 * gi + q];
     const typename Word<T>::Item it = Word<T>::item(rawb, row_slot, gi, col);
-    const int m = (int)(itw & 255) * 32 + lane;
-    if (m * U < e.zlen) Word<T>::build(it, m, Zs + e.zoff);
+    const int pu = (int)(itw & 255) * 32 + lane;  // unit pair: units 2pu, 2pu + 1
+    if (2 * pu * U < e.zlen) Word<T>::build2(it, pu, (2 * pu + 1) * U < e.zlen, Zs + e.zoff);
   }
 }
 
@@ -521,7 +537,7 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
           }
           e.zoff = (int16_t)words;
           e.zlen = (int16_t)zlen;
-          const int nseg = (zlen / U + 31) / 32;
+          const int nseg = (zlen / U + 63) / 64;
           for (int q = 0; q < nseg; ++q) {
             if (nitem >= kMaxItems) return P;
             gt.item[nitem++] = (uint16_t)((p << 8) | q);
