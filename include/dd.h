@@ -69,7 +69,10 @@ typedef struct {
   int32_t device;      /* CUDA device ordinal */
   int64_t max_cands;   /* device candidate buffer per chunk; 0 = default (1<<20) */
   uint32_t flags;      /* DD_FLAG_* */
-  int32_t reserved;
+  int32_t staging_threads; /* > 0: chunks in pageable host memory are first copied into a small
+                              pinned buffer per stream by this many host threads, then sent
+                              asynchronously (Sec. 2.1: pinned staging buffers filled by CPU
+                              threads); 0: pageable chunks are copied by the driver directly */
 } dd_opts_t;
 
 /* One single-pulse candidate (Sec. 2.2). */
@@ -115,6 +118,9 @@ int dd_plan_info(dd_plan_t plan, int64_t* overlap, int32_t* ntrials, const int32
  *   chunk       : time-major uint8 [nsamp][nchans]; a host pointer (pinned memory gives
  *                 asynchronous copies, Sec. 2.1) or a device pointer. Read-only; it must stay
  *                 valid and unchanged until this chunk's dd_candidates returns or dd_sync.
+ *                 With opts.staging_threads > 0 a pageable chunk is copied into the slot's
+ *                 pinned staging buffer before dd_run returns (the host copy of the next chunk
+ *                 overlaps the GPU work of this one) and may be reused as soon as it returns.
  *   nsamp       : new samples, 0 < nsamp <= chunk_len, a multiple of the largest decimation
  *   cuda_stream : NULL = the plan's own streams (chunk k runs on stream k mod n_streams);
  *                 otherwise every stage of this chunk is enqueued on that cudaStream_t.
@@ -213,6 +219,61 @@ int dd_sps_static(const int32_t* series, int32_t n_trials, int64_t n, int64_t st
 
 /* dd_plan_destroy -- wait for the plan's work and free everything it allocated. NULL is a no-op. */
 void dd_plan_destroy(dd_plan_t plan);
+
+/* ---------------------------------------------------------------- serving
+ * Many beams, each with a plan of its own, whose chunks arrive at arbitrary times (Sec. 1: work
+ * split over CUDA streams, applied across beams; Sec. 2.2: every buffer allocated when a beam is
+ * planned). A dispatcher thread owned by the server makes every plan call: a submitted chunk
+ * waits in its beam's queue and is started, in arrival order, as soon as fewer than
+ * max_inflight chunks are on the GPU and its beam has a free stream slot; chunks of different
+ * beams then run concurrently, each beam on its own streams, and a chunk gives the same
+ * candidates as it would with its beam alone. */
+typedef struct dd_server_s* dd_server_t;
+
+typedef struct {
+  int64_t ticket;    /* from dd_serve_submit */
+  int32_t beam;
+  int32_t status;    /* DD_OK or the error of dd_run / sps_run / dd_candidates */
+  int64_t seq;       /* chunk number within its beam */
+  int64_t ncands;    /* candidates found (those beyond cap are counted, not copied) */
+  double queue_ms;   /* submission -> start on the GPU */
+  double latency_ms; /* submission -> candidates in the caller's buffer */
+} dd_serve_result_t;
+
+/* dd_serve_create -- start a server on `device` that keeps at most max_inflight chunks on the
+ * GPU and accepts beams whose plans fit hbm_budget_bytes of device memory in total.
+ * Errors: DD_ERR_ARG. */
+int dd_serve_create(int32_t max_inflight, int64_t hbm_budget_bytes, int32_t device,
+                    dd_server_t* out);
+
+/* dd_serve_add_beam -- plan a beam (arguments as in dd_plan; opts->device is ignored, the
+ * server's device is used) and its search (widths, threshold as in sps_run). *beam receives its
+ * index. Errors: those of dd_plan; DD_ERR_NOMEM when the plan would exceed the HBM budget
+ * (the plan is released again). */
+int dd_serve_add_beam(dd_server_t server, const double* freqs_mhz, int32_t nchans,
+                      double tsamp_s, const dd_range_t* ranges, int32_t nranges,
+                      const dd_opts_t* opts, const int32_t* widths, int32_t nwidths,
+                      float threshold, int32_t* beam);
+
+/* dd_serve_submit -- queue the next chunk of a beam (as dd_run: time-major uint8
+ * [nsamp][nchans], host or device memory, caller-owned and unchanged until its result is
+ * polled). The chunk's candidates are copied to out (host, cap entries, sorted as by
+ * dd_candidates) before its result is reported. Returns without waiting (it may wait briefly
+ * while the dispatcher holds the server's lock). Errors: DD_ERR_ARG. */
+int dd_serve_submit(dd_server_t server, int32_t beam, const uint8_t* chunk, int64_t nsamp,
+                    dd_cand_t* out, int64_t cap, int64_t* ticket);
+
+/* dd_serve_poll -- take up to max finished results (oldest first), waiting up to timeout_ms
+ * for the first when none is ready (0: do not wait). *n receives the number taken. */
+int dd_serve_poll(dd_server_t server, dd_serve_result_t* out, int32_t max, int32_t* n,
+                  int64_t timeout_ms);
+
+/* dd_serve_pending -- chunks queued but not started, and chunks on the GPU. */
+int dd_serve_pending(dd_server_t server, int64_t* queued, int32_t* inflight);
+
+/* dd_serve_destroy -- stop the dispatcher (queued chunks are dropped, chunks on the GPU
+ * finish) and release every beam's plan. NULL is a no-op. */
+void dd_serve_destroy(dd_server_t server);
 
 /* dd_last_error -- message of the calling thread's last error ("" if none). Library-owned. */
 const char* dd_last_error(void);

@@ -26,7 +26,9 @@ DD_FLAG_TIMING = 1
 DD_FLAG_NAIVE = 2
 
 EXPORTS = ("dd_plan", "dd_plan_info", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
-           "dd_stats", "dd_sps_static", "dd_plan_destroy", "dd_last_error")
+           "dd_stats", "dd_sps_static", "dd_serve_create", "dd_serve_add_beam", "dd_serve_submit",
+           "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_plan_destroy",
+           "dd_last_error")
 
 
 class dd_range_t(ctypes.Structure):
@@ -38,7 +40,13 @@ class dd_opts_t(ctypes.Structure):
     _fields_ = [("chunk_len", ctypes.c_int64), ("n_streams", ctypes.c_int32),
                 ("max_width", ctypes.c_int32), ("peak_block", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("max_cands", ctypes.c_int64),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("staging_threads", ctypes.c_int32)]
+
+
+class dd_serve_result_t(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("beam", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("seq", ctypes.c_int64), ("ncands", ctypes.c_int64), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
 
 
 CAND_DTYPE = np.dtype([("trial", "<i4"), ("range", "<i4"), ("t_start", "<i8"), ("width", "<i4"),
@@ -76,10 +84,19 @@ def lib() -> ctypes.CDLL:
                                     vp, vp]
         L.dd_plan_destroy.argtypes = [vp]
         L.dd_plan_destroy.restype = None
+        L.dd_serve_create.argtypes = [i32, i64, i32, P(vp)]
+        L.dd_serve_add_beam.argtypes = [vp, vp, i32, f64, vp, i32, P(dd_opts_t), vp, i32, f32,
+                                        P(i32)]
+        L.dd_serve_submit.argtypes = [vp, i32, vp, i64, vp, i64, P(i64)]
+        L.dd_serve_poll.argtypes = [vp, vp, i32, P(i32), i64]
+        L.dd_serve_pending.argtypes = [vp, P(i64), P(i32)]
+        L.dd_serve_destroy.argtypes = [vp]
+        L.dd_serve_destroy.restype = None
         L.dd_last_error.argtypes = []
         L.dd_last_error.restype = ctypes.c_char_p
-        for name in EXPORTS[:-2]:
-            getattr(L, name).restype = ctypes.c_int
+        for name in EXPORTS:
+            if name not in ("dd_plan_destroy", "dd_serve_destroy", "dd_last_error"):
+                getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -107,13 +124,13 @@ def _ptr(a) -> int:
 
 def dd_plan(freqs_mhz, tsamp_s: float, ranges, chunk_len: int, n_streams: int = 1,
             max_width: int = 256, peak_block: int = 32, device: int = 0, max_cands: int = 0,
-            flags: int = 0) -> int:
+            flags: int = 0, staging_threads: int = 0) -> int:
     """Create a plan; ``ranges`` rows are (dm_start, dm_step, n_trials, decimation)."""
     f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
     rr = (dd_range_t * len(ranges))(*[dd_range_t(float(r[0]), float(r[1]), int(r[2]), int(r[3]))
                                       for r in ranges])
     o = dd_opts_t(int(chunk_len), int(n_streams), int(max_width), int(peak_block), int(device),
-                  int(max_cands), int(flags), 0)
+                  int(max_cands), int(flags), int(staging_threads))
     h = ctypes.c_void_p()
     _check(lib().dd_plan(f.ctypes.data, f.size, float(tsamp_s), ctypes.addressof(rr), len(ranges),
                          ctypes.byref(o), ctypes.byref(h)))
@@ -223,6 +240,72 @@ class Plan:
         if self.h:
             dd_plan_destroy(self.h)
             self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop over many beams (dd_serve_*): submit chunks as they arrive, poll results."""
+
+    def __init__(self, max_inflight: int, hbm_budget_bytes: int, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().dd_serve_create(int(max_inflight), int(hbm_budget_bytes), int(device),
+                                     ctypes.byref(h)))
+        self.h = h.value
+        self._keep = {}  # ticket -> (chunk, out buffer) kept alive until polled
+
+    def add_beam(self, freqs_mhz, tsamp_s, ranges, chunk_len, widths, threshold, n_streams=2,
+                 max_width=None, peak_block=32, max_cands=0, flags=0, staging_threads=0) -> int:
+        f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+        rr = (dd_range_t * len(ranges))(*[dd_range_t(float(r[0]), float(r[1]), int(r[2]),
+                                                     int(r[3])) for r in ranges])
+        w = np.ascontiguousarray(widths, dtype=np.int32)
+        o = dd_opts_t(int(chunk_len), int(n_streams), int(max_width or int(w.max())),
+                      int(peak_block), 0, int(max_cands), int(flags), int(staging_threads))
+        b = ctypes.c_int32()
+        _check(lib().dd_serve_add_beam(self.h, f.ctypes.data, f.size, float(tsamp_s),
+                                       ctypes.addressof(rr), len(ranges), ctypes.byref(o),
+                                       w.ctypes.data, w.size, ctypes.c_float(threshold),
+                                       ctypes.byref(b)))
+        return b.value
+
+    def submit(self, beam: int, chunk, nsamp=None, cap: int = 1 << 16) -> int:
+        n = chunk.shape[0] if nsamp is None else nsamp
+        out = np.zeros(cap, dtype=CAND_DTYPE)
+        t = ctypes.c_int64()
+        _check(lib().dd_serve_submit(self.h, int(beam), _ptr(chunk), int(n), out.ctypes.data,
+                                     int(cap), ctypes.byref(t)))
+        self._keep[t.value] = (chunk, out)
+        return t.value
+
+    def poll(self, max_results: int = 64, timeout_ms: int = 0):
+        """Finished results as (dd_serve_result_t fields dict, candidates array)."""
+        buf = (dd_serve_result_t * max_results)()
+        n = ctypes.c_int32()
+        _check(lib().dd_serve_poll(self.h, ctypes.addressof(buf), int(max_results),
+                                   ctypes.byref(n), int(timeout_ms)))
+        out = []
+        for k in range(n.value):
+            r = buf[k]
+            d = {f: getattr(r, f) for f, _ in dd_serve_result_t._fields_}
+            _, cands = self._keep.pop(r.ticket, (None, None))
+            out.append((d, None if cands is None else cands[:min(r.ncands, cands.size)]))
+        return out
+
+    def pending(self):
+        q, i = ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().dd_serve_pending(self.h, ctypes.byref(q), ctypes.byref(i)))
+        return q.value, i.value
+
+    def close(self):
+        if self.h:
+            lib().dd_serve_destroy(self.h)
+            self.h = 0
+            self._keep.clear()
 
     def __del__(self):
         try:

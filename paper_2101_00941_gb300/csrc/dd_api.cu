@@ -8,7 +8,11 @@
 //   device in `hist`; chunk k loads it after chunk k-1 saved it (one event per plan), so the
 //   only cross-stream dependency is this short device-to-device copy.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -67,6 +71,70 @@ int wait_event(cudaEvent_t ev, int64_t timeout_ms) {
   }
 }
 
+// Host threads that split one host-to-host copy (pageable chunk -> pinned staging buffer)
+// between them (Sec. 2.1: CPU threads filling small pinned buffers). copy() returns when every
+// part is done.
+class StagingPool {
+ public:
+  explicit StagingPool(int n) {
+    for (int i = 0; i < n; ++i) threads_.emplace_back([this, i] { run(i); });
+  }
+  ~StagingPool() {
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+  }
+  void copy(uint8_t* dst, const uint8_t* src, size_t bytes) {
+    std::unique_lock<std::mutex> l(mu_);
+    dst_ = dst;
+    src_ = src;
+    bytes_ = bytes;
+    pending_ = (int)threads_.size();
+    ++gen_;
+    cv_.notify_all();
+    done_cv_.wait(l, [this] { return pending_ == 0; });
+  }
+
+ private:
+  void run(int i) {
+    uint64_t seen = 0;
+    for (;;) {
+      uint8_t* dst;
+      const uint8_t* src;
+      size_t bytes;
+      {
+        std::unique_lock<std::mutex> l(mu_);
+        cv_.wait(l, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        dst = dst_;
+        src = src_;
+        bytes = bytes_;
+      }
+      const size_t n = threads_.size();
+      const size_t part = (bytes + n - 1) / n;
+      const size_t b0 = std::min(bytes, part * (size_t)i), b1 = std::min(bytes, b0 + part);
+      if (b1 > b0) std::memcpy(dst + b0, src + b0, b1 - b0);
+      {
+        std::lock_guard<std::mutex> l(mu_);
+        if (--pending_ == 0) done_cv_.notify_all();
+      }
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  bool stop_ = false;
+  uint64_t gen_ = 0;
+  int pending_ = 0;
+  uint8_t* dst_ = nullptr;
+  const uint8_t* src_ = nullptr;
+  size_t bytes_ = 0;
+};
+
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaStream_t used = nullptr;  // stream the current chunk was enqueued on
@@ -80,6 +148,8 @@ struct Slot {
   unsigned long long* h_count = nullptr;  // pinned copy of d_count
   cudaEvent_t ev_free = nullptr;          // last work enqueued for this slot
   cudaEvent_t ev_sps = nullptr;           // search + count readback done
+  uint8_t* h_stage = nullptr;             // pinned staging buffer (staging_threads > 0)
+  cudaEvent_t ev_staged = nullptr;        // copy out of h_stage finished
   int64_t seq = -1, T = 0, n = 0, lo = 0, hi = 0;
   bool searched = false;
 };
@@ -125,6 +195,7 @@ struct dd_plan_s {
   // dedispersion timing (DD_FLAG_TIMING): every launch is bracketed by an event pair; the pairs
   // are turned into [start, end) intervals against a common reference event and merged, so that
   // launches of different chunks running at the same time on different streams count once
+  StagingPool* pool = nullptr;     // staging_threads > 0
   std::vector<cudaEvent_t> tev;
   int64_t tev_used = 0;
   cudaEvent_t tref = nullptr;
@@ -143,7 +214,10 @@ void free_plan(dd_plan_s* p) {
     if (s.stream) cudaStreamSynchronize(s.stream);
   }
   if (p->io) cudaStreamSynchronize(p->io);
+  delete p->pool;
   for (auto& s : p->slots) {
+    cudaFreeHost(s.h_stage);
+    if (s.ev_staged) cudaEventDestroy(s.ev_staged);
     cudaFree(s.staging);
     cudaFree(s.ring1);
     for (auto* r : s.ringd) cudaFree(r);
@@ -237,6 +311,17 @@ int timing_end(dd_plan_s* p, cudaStream_t st, int64_t slot) {
 
 namespace ddk {
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int chunk_state(dd_plan_s* p, int64_t seq) {
+  const int64_t S = (int64_t)p->slots.size();
+  if (seq < 0 || seq >= p->next_seq || seq < p->next_seq - S) return DD_ERR_STATE;
+  Slot& s = p->slots[seq % S];
+  if (s.seq != seq || !s.searched) return DD_ERR_STATE;
+  const cudaError_t e = cudaEventQuery(s.ev_sps);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return fail(DD_ERR_CUDA, "chunk state: %s", cudaGetErrorString(e));
+}
 }  // namespace ddk
 
 extern "C" {
@@ -284,6 +369,8 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
   if ((int64_t)nchans * 255 * std::max(dmax, o.max_width) >= (int64_t(1) << 31))
     return fail(DD_ERR_ARG, "nchans*255*max(width, decimation) must be < 2^31 (int32 sums)");
   if (o.max_cands < 0) return fail(DD_ERR_ARG, "max_cands < 0");
+  if (o.staging_threads < 0 || o.staging_threads > 64)
+    return fail(DD_ERR_ARG, "staging_threads %d outside 0..64", o.staging_threads);
 
   int ndev = 0;
   DD_CK(cudaGetDeviceCount(&ndev));
@@ -455,6 +542,15 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     DD_TRY(dalloc(&s.cands, sizeof(dd_cand_t) * (size_t)p->opts.max_cands, "candidates"));
     DD_TRY(dalloc(&s.d_count, 2 * sizeof(unsigned long long), "count"));
     DD_TRYCK(cudaMemset(s.d_count, 0, 2 * sizeof(unsigned long long)));
+    if (o.staging_threads > 0) {
+      if (cudaMallocHost((void**)&s.h_stage, (size_t)p->L * nchans) != cudaSuccess) {
+        cudaGetLastError();
+        s.h_stage = nullptr;
+        free_plan(p);
+        return fail(DD_ERR_NOMEM, "pinned staging buffer");
+      }
+      DD_TRYCK(cudaEventCreateWithFlags(&s.ev_staged, cudaEventDisableTiming));
+    }
     if (cudaMallocHost((void**)&s.h_count, 2 * sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       s.h_count = nullptr;
@@ -462,6 +558,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
       return fail(DD_ERR_NOMEM, "pinned count");
     }
   }
+  if (o.staging_threads > 0) p->pool = new StagingPool(o.staging_threads);
   if (o.flags & DD_FLAG_TIMING) {
     p->tev.resize(2 * 1024);
     for (auto& e : p->tev) DD_TRYCK(cudaEventCreate(&e));
@@ -500,7 +597,16 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
   cudaPointerAttributes attr;
   DD_CK(cudaPointerGetAttributes(&attr, chunk));
   const uint8_t* src = chunk;
-  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+  if (attr.type == cudaMemoryTypeUnregistered && p->pool) {
+    // pageable chunk: host threads copy it into the slot's pinned buffer (once the previous
+    // copy out of that buffer has finished), then it goes to the device asynchronously
+    int rc = wait_event(s.ev_staged, 0);
+    if (rc) return rc;
+    p->pool->copy(s.h_stage, chunk, (size_t)nsamp * p->C);
+    DD_CK(cudaMemcpyAsync(s.staging, s.h_stage, (size_t)nsamp * p->C, cudaMemcpyHostToDevice, st));
+    DD_CK(cudaEventRecord(s.ev_staged, st));
+    src = s.staging;
+  } else if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
     DD_CK(cudaMemcpyAsync(s.staging, chunk, (size_t)nsamp * p->C, cudaMemcpyHostToDevice, st));
     src = s.staging;
   }

@@ -105,6 +105,10 @@ cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st
 // Record `msg` as the calling thread's last error (dd_last_error) and return `code`.
 int report_error(int code, const char* msg);
 
+// 1 when chunk `seq` of the plan has been searched and its candidates are ready, 0 while its
+// work is pending, DD_ERR_STATE if it is not a searched chunk still held by the plan.
+int chunk_state(dd_plan_s* plan, int64_t seq);
+
 // ---- launchers (dd_kernels.cu); each returns the cudaGetLastError() of its launch
 cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t c4, double fref,
                                double tsamp, const ShiftRange* ranges, int32_t nranges,

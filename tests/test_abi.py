@@ -45,7 +45,7 @@ def test_header_structs_match_binding():
 
 def _opts(**kw):
     o = dict(chunk_len=4096, n_streams=2, max_width=32, peak_block=32, device=0, max_cands=0,
-             flags=0, reserved=0)
+             flags=0, staging_threads=0)
     o.update(kw)
     return dd.dd_opts_t(**o)
 
@@ -64,7 +64,7 @@ def _plan(lib, nchans=16, freqs=None, ranges=((0.0, 1.0, 8, 1),), **kw):
     dict(max_width=0), dict(peak_block=3), dict(peak_block=64),
     dict(ranges=((0.0, 1.0, 8, 3),)), dict(ranges=((0.0, 1.0, 0, 1),)),
     dict(ranges=((-1.0, 1.0, 8, 1),)), dict(freqs=[1500.0, -1.0] + [1400.0] * 14),
-    dict(nchans=8192, max_width=1024),
+    dict(nchans=8192, max_width=1024), dict(staging_threads=-1), dict(staging_threads=65),
 ])
 def test_invalid_plans_are_rejected_before_any_gpu_work(lib, kw):
     assert _plan(lib, **kw) == dd.DD_ERR_ARG

@@ -36,15 +36,16 @@ def _as_input(part, kind):
         return torch.from_numpy(part).cuda()
     if kind == "pinned":
         return torch.from_numpy(part).pin_memory()
-    return np.ascontiguousarray(part)
+    return np.ascontiguousarray(part)  # pageable (copied by the driver or by staging threads)
 
 
 def run_gpu(w, x, chunk_sizes, n_streams, kind="device", flags=0, want_series=True,
             chunk_len=None, trials=None):
     ranges = w.ranges_array()
     L = chunk_len or int(-(-max(chunk_sizes) // 256) * 256)
+    staging = 4 if kind == "staged" else 0
     plan = dd.Plan(w.freqs(), w.tsamp, ranges, L, n_streams=n_streams, max_width=max(w.widths),
-                   peak_block=32, flags=flags)
+                   peak_block=32, flags=flags, staging_threads=staging)
     out = []
     T = 0
     try:
@@ -151,7 +152,7 @@ def test_one_thread_per_output_kernel_matches():
     check(w, x, [4096] * 4, 2, flags=dd.DD_FLAG_NAIVE)
 
 
-@pytest.mark.parametrize("kind", ["pinned", "pageable"])
+@pytest.mark.parametrize("kind", ["pinned", "pageable", "staged"])
 def test_ragged_channels_host_input(kind):
     w = _small_multirange(nchans=98, nsamp=1 << 14, npulses=3)
     x = w.generate(_arrivals(w))
@@ -159,9 +160,12 @@ def test_ragged_channels_host_input(kind):
 
 
 def test_input_kinds_give_identical_results():
+    """Sec. 2.1: pinned, pageable and pageable-through-pinned-staging inputs give the same
+    results as device-resident input."""
     w = _small_multirange(nsamp=1 << 14)
     x = w.generate(_arrivals(w))
-    res = [run_gpu(w, x, [4096] * 4, 2, kind=k)[0] for k in ("device", "pinned", "pageable")]
+    res = [run_gpu(w, x, [4096] * 4, 2, kind=k)[0]
+           for k in ("device", "pinned", "pageable", "staged")]
     for other in res[1:]:
         for (sa, ca), (sb, cb) in zip(res[0], other):
             np.testing.assert_array_equal(ca, cb)
