@@ -245,6 +245,108 @@ def main_reference(args):
     return 0
 
 
+def serve_workload(args):
+    """16 beams, 4096 channels, the full DM 0-1000 plan, chunks of 2^16 samples (10% 2^17)
+    arriving as Poisson streams; the served loop against the plain per-chunk loop."""
+    import torch
+
+    import paper_2101_00941_gb300 as dd
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    dd.build()
+    nbeams, cadence_s = args.beams, (1 << 16) * 64e-6
+    rng = np.random.default_rng(configs.SEED_BASE + 3)
+    beams, pools = [], []
+    for b in range(nbeams):
+        w = configs.mid(nsamp=(1 << 17) * 2, chunk_len=1 << 17, n_streams=2, npulses=5,
+                        index=3, beam=b)
+        beams.append(w)
+        # a pool of two distinct seeded 2^17-sample chunks per beam, reused cyclically
+        x = torch.empty(((1 << 17) * 2, w.nchans), dtype=torch.uint8, pin_memory=True)
+        w.generate(pulse_offsets(w), out=x.numpy())
+        pools.append(x)
+    # arrivals: per beam a Poisson stream at cadence/speedup; 10% of chunks are 2^17 long
+    arr = []
+    for b in range(nbeams):
+        t = 0.0
+        for k in range(args.chunks_per_beam):
+            t += rng.exponential(cadence_s / args.speedup)
+            n = (1 << 17) if rng.random() < 0.1 else (1 << 16)
+            arr.append((t, b, k, n))
+    arr.sort()
+    outs = {b: 0 for b in range(nbeams)}
+
+    def view(b, k, n):
+        base = (k % 2) * (1 << 17)
+        return pools[b][base:base + n]
+
+    def outputs(w, n, O, T):
+        lo, hi = max(0, T - O), max(0, T + n - O)
+        return sum(r.n_trials * ((hi // r.decimation) - (lo // r.decimation)) for r in w.ranges)
+
+    # ---- served loop
+    srv = dd.Server(max_inflight=args.inflight, hbm_budget_bytes=200 << 30, device=dev)
+    ids = [srv.add_beam(w.freqs(), w.tsamp, w.ranges_array(), 1 << 17, w.widths, w.threshold,
+                        n_streams=2) for w in beams]
+    O = dd.Plan(beams[0].freqs(), beams[0].tsamp, beams[0].ranges_array(), 1 << 17).O
+    lat, done_outputs, T = [], 0, {b: 0 for b in range(nbeams)}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pending = 0
+    for (ta, b, k, n) in arr:
+        while time.perf_counter() - t0 < ta:
+            for r, _ in srv.poll(64, timeout_ms=0):
+                lat.append(r["latency_ms"])
+                pending -= 1
+            time.sleep(0.0005)
+        srv.submit(ids[b], view(b, k, n), n)
+        done_outputs += outputs(beams[b], n, O, T[b])
+        T[b] += n
+        pending += 1
+    while pending > 0:
+        for r, _ in srv.poll(64, timeout_ms=1000):
+            lat.append(r["latency_ms"])
+            pending -= 1
+    served_s = time.perf_counter() - t0
+    srv.close()
+    # ---- plain per-chunk loop: one stream per beam, each chunk copied, dedispersed,
+    #      searched and synchronised before the next one starts
+    plans = [dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 1 << 17, n_streams=1,
+                     max_width=max(w.widths)) for w in beams]
+    plain_lat = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (ta, b, k, n) in arr:
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0005)
+        t_arr = t0 + ta
+        p = plans[b]
+        p.run(view(b, k, n), n)
+        p.search(beams[b].widths, beams[b].threshold)
+        p.candidates()
+        plain_lat.append(1e3 * (time.perf_counter() - t_arr))
+    plain_s = time.perf_counter() - t0
+    for p in plans:
+        p.close()
+    obs = sum(n for (_, _, _, n) in arr) * 64e-6
+    line = {
+        "metric": METRIC, "value": done_outputs / served_s, "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * served_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32", "data": "synthetic",
+        "config": {"workload": f"serve_{nbeams}beams_4096ch_2e16", "beams": nbeams,
+                   "chunks": len(arr), "arrival_speedup": args.speedup,
+                   "max_inflight": args.inflight, "input": "pinned host, 2 chunks per beam reused"},
+        "real_time_factor": obs / served_s,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "plain_loop": {"value": done_outputs / plain_s, "real_time_factor": obs / plain_s,
+                       "latency_ms": {"p50": float(np.percentile(plain_lat, 50)),
+                                      "p99": float(np.percentile(plain_lat, 99))}},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main(args):
     import torch
 
@@ -336,5 +438,13 @@ if __name__ == "__main__":
     ap.add_argument("--nsamp", type=int, default=1 << 20,
                     help="samples per beam (a multiple of 2^17; smaller only for profiler captures)")
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the chunks rotate over")
+    ap.add_argument("--workload", choices=["mid", "serve"], default="mid")
+    ap.add_argument("--beams", type=int, default=16, help="serve: beams")
+    ap.add_argument("--chunks-per-beam", type=int, default=6, help="serve: chunks per beam")
+    ap.add_argument("--speedup", type=float, default=8.0,
+                    help="serve: arrival rate relative to real time (1 = 4.19 s cadence)")
+    ap.add_argument("--inflight", type=int, default=8, help="serve: chunks on the GPU at once")
     a = ap.parse_args()
-    sys.exit(main_reference(a) if a.impl == "reference" else main(a))
+    if a.impl == "reference":
+        sys.exit(main_reference(a))
+    sys.exit(serve_workload(a) if a.workload == "serve" else main(a))

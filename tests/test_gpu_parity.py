@@ -282,3 +282,17 @@ def test_timing_and_launch_counters():
         assert ms > 0 and nlaunch == live
     finally:
         plan.close()
+
+
+def test_out_of_core_shape_from_pageable_memory_through_staging():
+    """8192 channels, 1000-1500 MHz, 50 us, DM 0-3000 with x1..x16 decimation (overlap ~138k
+    samples), two 2^18-sample chunks from pageable memory through the pinned staging threads;
+    sampled trials of every range, bit-exact series and matching candidates."""
+    w = configs.out_of_core(nsamp=1 << 19)
+    w.chunk_len = 1 << 18
+    w.n_streams = 2
+    x = w.generate(_arrivals(w))
+    rng = np.random.default_rng(8)
+    trials = [sorted({0, r.n_trials - 1} | set(int(v) for v in rng.integers(0, r.n_trials, 2)))
+              for r in w.ranges]
+    assert check(w, x, [w.chunk_len, w.chunk_len], 2, kind="staged", trials=trials) >= 0
