@@ -48,6 +48,8 @@ extern "C" {
 /* Plan option flags. */
 #define DD_FLAG_TIMING 1u   /* bracket every dedispersion launch with CUDA events (dd_stats) */
 #define DD_FLAG_NAIVE 2u    /* use the one-thread-per-output dedispersion kernel (testing aid) */
+#define DD_FLAG_DEVICE_INPUT 4u /* chunks are always in device memory: no staging buffer is
+                                   allocated and host chunks are refused (DD_ERR_ARG) */
 
 typedef struct dd_plan_s* dd_plan_t;
 
@@ -267,6 +269,53 @@ int dd_serve_submit(dd_server_t server, int32_t beam, const uint8_t* chunk, int6
  * for the first when none is ready (0: do not wait). *n receives the number taken. */
 int dd_serve_poll(dd_server_t server, dd_serve_result_t* out, int32_t max, int32_t* n,
                   int64_t timeout_ms);
+
+/* ---------------------------------------------------------------- batches
+ * Many beams of uneven length and channel count processed in one step, each from its first
+ * sample: chunks are enqueued round-robin over the beams (each beam with a plan of its own and
+ * its own streams), so the beams' work overlaps on the device; every (beam, chunk) keeps its own
+ * candidates. DD_BATCH_GRAPH captures the step once as a CUDA graph that every dd_batch_run
+ * replays (the inputs stay at their device addresses; refill them between steps).
+ * DD_BATCH_AUTOTUNE picks the time tile of every plan's ranges by timing the candidates. */
+#define DD_BATCH_GRAPH 1u
+#define DD_BATCH_AUTOTUNE 2u
+
+typedef struct dd_batch_s* dd_batch_t;
+
+typedef struct {
+  const double* freqs_mhz; /* host [nchans] */
+  int32_t nchans;
+  int32_t pad;
+  double tsamp_s;
+  int64_t nsamp;           /* samples of the beam, a multiple of the largest decimation */
+  const uint8_t* input;    /* DEVICE time-major [nsamp][nchans], caller-owned */
+} dd_batch_beam_t;
+
+/* dd_batch_create -- plan every beam (ranges and opts shared; opts->chunk_len is the chunk
+ * length; DD_FLAG_TIMING is refused), allocate cap_per_chunk candidates for every (beam, chunk)
+ * and, with DD_BATCH_GRAPH, capture one step. Errors: those of dd_plan, DD_ERR_ARG,
+ * DD_ERR_NOMEM, DD_ERR_CUDA. */
+int dd_batch_create(int32_t nbeams, const dd_batch_beam_t* beams, const dd_range_t* ranges,
+                    int32_t nranges, const dd_opts_t* opts, const int32_t* widths,
+                    int32_t nwidths, float threshold, int64_t cap_per_chunk, uint32_t flags,
+                    dd_batch_t* out);
+
+/* dd_batch_run -- enqueue one step (asynchronous); dd_batch_wait waits for it (bounded). */
+int dd_batch_run(dd_batch_t batch);
+int dd_batch_wait(dd_batch_t batch, int64_t timeout_ms);
+
+/* dd_batch_info -- chunks of a beam, its DM-trial*samples per step, and the time tile chosen
+ * for its first range (0: the simple kernel). */
+int dd_batch_info(dd_batch_t batch, int32_t beam, int64_t* nchunks, int64_t* outputs,
+                  int32_t* tile_samples);
+
+/* dd_batch_candidates -- after dd_batch_wait: the candidates of one (beam, chunk), sorted as by
+ * dd_candidates. Errors: DD_ERR_ARG, DD_ERR_STATE (no finished step), DD_ERR_CAP. */
+int dd_batch_candidates(dd_batch_t batch, int32_t beam, int64_t chunk, dd_cand_t* out,
+                        int64_t cap, int64_t* ncands);
+
+/* dd_batch_destroy -- wait and release everything. NULL is a no-op. */
+void dd_batch_destroy(dd_batch_t batch);
 
 /* dd_serve_pending -- chunks queued but not started, and chunks on the GPU. */
 int dd_serve_pending(dd_server_t server, int64_t* queued, int32_t* inflight);

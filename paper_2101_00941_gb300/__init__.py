@@ -24,11 +24,15 @@ DD_ERR_CAP = -5
 DD_ERR_STATE = -6
 DD_FLAG_TIMING = 1
 DD_FLAG_NAIVE = 2
+DD_FLAG_DEVICE_INPUT = 4
+DD_BATCH_GRAPH = 1
+DD_BATCH_AUTOTUNE = 2
 
 EXPORTS = ("dd_plan", "dd_plan_info", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
            "dd_stats", "dd_sps_static", "dd_serve_create", "dd_serve_add_beam", "dd_serve_submit",
-           "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_plan_destroy",
-           "dd_last_error")
+           "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_batch_create",
+           "dd_batch_run", "dd_batch_wait", "dd_batch_info", "dd_batch_candidates",
+           "dd_batch_destroy", "dd_plan_destroy", "dd_last_error")
 
 
 class dd_range_t(ctypes.Structure):
@@ -41,6 +45,11 @@ class dd_opts_t(ctypes.Structure):
                 ("max_width", ctypes.c_int32), ("peak_block", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("max_cands", ctypes.c_int64),
                 ("flags", ctypes.c_uint32), ("staging_threads", ctypes.c_int32)]
+
+
+class dd_batch_beam_t(ctypes.Structure):
+    _fields_ = [("freqs_mhz", ctypes.c_void_p), ("nchans", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("tsamp_s", ctypes.c_double), ("nsamp", ctypes.c_int64), ("input", ctypes.c_void_p)]
 
 
 class dd_serve_result_t(ctypes.Structure):
@@ -92,10 +101,19 @@ def lib() -> ctypes.CDLL:
         L.dd_serve_pending.argtypes = [vp, P(i64), P(i32)]
         L.dd_serve_destroy.argtypes = [vp]
         L.dd_serve_destroy.restype = None
+        L.dd_batch_create.argtypes = [i32, vp, vp, i32, P(dd_opts_t), vp, i32, f32, i64,
+                                      ctypes.c_uint32, P(vp)]
+        L.dd_batch_run.argtypes = [vp]
+        L.dd_batch_wait.argtypes = [vp, i64]
+        L.dd_batch_info.argtypes = [vp, i32, P(i64), P(i64), P(i32)]
+        L.dd_batch_candidates.argtypes = [vp, i32, i64, vp, i64, P(i64)]
+        L.dd_batch_destroy.argtypes = [vp]
+        L.dd_batch_destroy.restype = None
         L.dd_last_error.argtypes = []
         L.dd_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("dd_plan_destroy", "dd_serve_destroy", "dd_last_error"):
+            if name not in ("dd_plan_destroy", "dd_serve_destroy", "dd_batch_destroy",
+                            "dd_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -306,6 +324,65 @@ class Server:
             lib().dd_serve_destroy(self.h)
             self.h = 0
             self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many beams processed in one step (dd_batch_*). `beams`: list of (freqs, tsamp, device
+    uint8 tensor [nsamp][nchans]); the tensors must stay alive and in place."""
+
+    def __init__(self, beams, ranges, chunk_len, widths, threshold, n_streams=1,
+                 max_width=None, peak_block=32, cap_per_chunk=1 << 14, graph=False,
+                 autotune=False, device=0, flags=DD_FLAG_DEVICE_INPUT):
+        self._freqs = [np.ascontiguousarray(f, dtype=np.float64) for f, _, _ in beams]
+        self._inputs = [x for _, _, x in beams]
+        arr = (dd_batch_beam_t * len(beams))()
+        for k, (f, ts, x) in enumerate(beams):
+            arr[k] = dd_batch_beam_t(self._freqs[k].ctypes.data, int(self._freqs[k].size), 0,
+                                     float(ts), int(x.shape[0]), _ptr(x))
+        rr = (dd_range_t * len(ranges))(*[dd_range_t(float(r[0]), float(r[1]), int(r[2]),
+                                                     int(r[3])) for r in ranges])
+        w = np.ascontiguousarray(widths, dtype=np.int32)
+        o = dd_opts_t(int(chunk_len), int(n_streams), int(max_width or int(w.max())),
+                      int(peak_block), int(device), 0, int(flags), 0)
+        h = ctypes.c_void_p()
+        bf = (DD_BATCH_GRAPH if graph else 0) | (DD_BATCH_AUTOTUNE if autotune else 0)
+        _check(lib().dd_batch_create(len(beams), ctypes.addressof(arr), ctypes.addressof(rr),
+                                     len(ranges), ctypes.byref(o), w.ctypes.data, w.size,
+                                     ctypes.c_float(threshold), int(cap_per_chunk), bf,
+                                     ctypes.byref(h)))
+        self.h = h.value
+        self.cap = int(cap_per_chunk)
+        self.nbeams = len(beams)
+
+    def run(self):
+        _check(lib().dd_batch_run(self.h))
+
+    def wait(self, timeout_ms=0):
+        _check(lib().dd_batch_wait(self.h, int(timeout_ms)))
+
+    def info(self, beam):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().dd_batch_info(self.h, int(beam), ctypes.byref(a), ctypes.byref(b),
+                                   ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def candidates(self, beam, chunk):
+        out = np.zeros(self.cap, dtype=CAND_DTYPE)
+        n = ctypes.c_int64()
+        _check(lib().dd_batch_candidates(self.h, int(beam), int(chunk), out.ctypes.data,
+                                         self.cap, ctypes.byref(n)))
+        return out[:n.value]
+
+    def close(self):
+        if self.h:
+            lib().dd_batch_destroy(self.h)
+            self.h = 0
 
     def __del__(self):
         try:

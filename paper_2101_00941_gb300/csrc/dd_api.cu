@@ -312,6 +312,166 @@ int timing_end(dd_plan_s* p, cudaStream_t st, int64_t slot) {
 namespace ddk {
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+int plan_reset(dd_plan_s* p) {
+  DD_CK(cudaSetDevice(p->device));
+  for (auto& s : p->slots) {
+    DD_CK(cudaStreamSynchronize(s.stream));
+    if (s.used && s.used != s.stream) DD_CK(cudaStreamSynchronize(s.used));
+    s.seq = -1;
+    s.searched = false;
+    s.used = nullptr;
+  }
+  p->next_seq = 0;
+  p->T_total = 0;
+  return DD_OK;
+}
+
+void plan_streams(dd_plan_s* p, std::vector<cudaStream_t>* out) {
+  for (auto& s : p->slots) out->push_back(s.stream);
+}
+
+int64_t plan_outputs(dd_plan_s* p, int64_t nsamp) {
+  int64_t n = 0;
+  const int64_t hi = std::max<int64_t>(0, nsamp - p->O);
+  for (auto& r : p->ranges) n += (int64_t)r.n_trials * (hi / r.decimation);
+  return n;
+}
+
+int sps_enqueue(dd_plan_s* p, const int32_t* widths, int32_t nwidths, float threshold,
+                dd_cand_t* cands, unsigned long long* count, int64_t cap) {
+  if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
+  Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
+  if (s.searched) return fail(DD_ERR_STATE, "the latest chunk was already searched");
+  cudaStream_t st = s.used;
+  DD_CK(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+  for (size_t r = 0; r < p->ranges.size(); ++r) {
+    const int d = p->ranges[r].decimation;
+    ddk::SpsArgs a;
+    std::memset(&a, 0, sizeof a);
+    for (int k = 0; k < nwidths; ++k)
+      if (widths[k] >= d && widths[k] % d == 0) a.wd[a.nw++] = widths[k] / d;
+    a.n = (s.hi - s.lo) / d;
+    if (a.nw == 0 || a.n <= 0) continue;
+    a.y = s.series + p->series_off[r];
+    a.stride = p->series_stride[r];
+    a.mom = s.mom + p->row0[r];
+    a.n_trials = p->ranges[r].n_trials;
+    a.range = (int32_t)r;
+    a.d = d;
+    a.block = p->opts.peak_block;
+    a.J0 = s.lo / d;
+    a.hist = (int32_t)round_up(std::max(a.wd[a.nw - 1] - 1, 0), 256);
+    a.threshold = threshold;
+    a.cands = cands;
+    a.count = count;
+    a.cap = cap;
+    DD_CK(ddk::launch_sps(a, st));
+    p->launches += 1;
+  }
+  DD_CK(cudaEventRecord(s.ev_free, st));
+  s.searched = true;
+  return DD_OK;
+}
+
+// Time the tiled kernel of every range at each of its candidate tile sizes on the plan's own
+// buffers (contents irrelevant) and keep the fastest; the plan must be idle.
+int plan_autotune(dd_plan_s* p) {
+  DD_CK(cudaSetDevice(p->device));
+  Slot& s = p->slots[0];
+  cudaEvent_t e0, e1;
+  DD_CK(cudaEventCreate(&e0));
+  DD_CK(cudaEventCreate(&e1));
+  int rc = DD_OK;
+  for (size_t r = 0; r < p->ranges.size() && rc == DD_OK; ++r) {
+    RangeKernel& cur = p->rk[r];
+    if (!cur.tiled) continue;
+    const int d = p->ranges[r].decimation;
+    const bool u16 = d > 1;
+    const int l = ilog2(d);
+    std::vector<int32_t> tab((size_t)p->ranges[r].n_trials * p->C4);
+    if (cudaMemcpy(tab.data(), p->d_shifts + (int64_t)p->row0[r] * p->C4,
+                   sizeof(int32_t) * tab.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rc = fail(DD_ERR_CUDA, "autotune: reading the delay table failed");
+      break;
+    }
+    float best_ms = 1e30f;
+    RangeKernel best = cur;
+    for (int choice = 0; choice < 2; ++choice) {
+      const int tt = ddk::tiled_tile_samples(u16, choice);
+      RangeKernel k = cur;
+      ddk::TiledPlan tp;
+      if (tt == cur.tt) {
+        k = cur;
+      } else {
+        tp = ddk::tiled_plan(tab.data(), p->ranges[r].n_trials, p->C4, u16, tt);
+        if (!tp.ok) continue;
+        if (dalloc(&k.d_tabs, tp.tab_bytes, "delay-class tables")) {
+          rc = DD_ERR_NOMEM;
+          break;
+        }
+        if (cudaMemcpy(k.d_tabs, tp.tabs.data(), tp.tab_bytes, cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            ddk::prepare_tiled(u16, tt, tp.smem) != cudaSuccess) {
+          cudaFree(k.d_tabs);
+          rc = fail(DD_ERR_CUDA, "autotune: set-up failed");
+          break;
+        }
+        k.tt = tt;
+        k.row_slot = tp.row_slot;
+        k.zcap = tp.zcap;
+        k.smem = tp.smem;
+      }
+      ddk::TiledArgs A;
+      A.xd = (l == 0) ? (const void*)s.ring1 : (const void*)s.ringd[l];
+      A.xd_stride = (l == 0) ? p->R1 : p->Rd[l];
+      A.m0 = 0;
+      A.nout = std::max<int64_t>(1, (p->L - p->O + p->H) / d);
+      A.nout = std::min<int64_t>(A.nout, p->L / d);
+      A.y = s.series + p->series_off[r];
+      A.y_stride = p->series_stride[r];
+      A.mom = s.mom + p->row0[r];
+      A.shifts = p->d_shifts + (int64_t)p->row0[r] * p->C4;
+      A.n_trials = p->ranges[r].n_trials;
+      A.c4 = p->C4;
+      A.row_slot = k.row_slot;
+      A.zcap = k.zcap;
+      A.tabs = k.d_tabs;
+      A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
+      float ms = 0;
+      cudaError_t e = ddk::launch_tiled(A, u16, k.tt, s.stream);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s.stream);
+      if (e == cudaSuccess) e = ddk::launch_tiled(A, u16, k.tt, s.stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s.stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        if (k.d_tabs != cur.d_tabs) cudaFree(k.d_tabs);
+        rc = fail(DD_ERR_CUDA, "autotune: timing launch failed: %s", cudaGetErrorString(e));
+        break;
+      }
+      if (ms < best_ms) {
+        if (best.d_tabs != cur.d_tabs) cudaFree(best.d_tabs);
+        best_ms = ms;
+        best = k;
+      } else if (k.d_tabs != cur.d_tabs) {
+        cudaFree(k.d_tabs);
+      }
+    }
+    if (rc != DD_OK) break;
+    if (best.d_tabs != cur.d_tabs) {
+      cudaFree(cur.d_tabs);
+      cur = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DD_CK(cudaMemsetAsync(s.d_count, 0, 2 * sizeof(unsigned long long), s.stream));
+  DD_CK(cudaStreamSynchronize(s.stream));
+  return rc;
+}
+
+int range_tile(dd_plan_s* p, int r) { return p->rk[r].tiled ? p->rk[r].tt : 0; }
+
 int chunk_state(dd_plan_s* p, int64_t seq) {
   const int64_t S = (int64_t)p->slots.size();
   if (seq < 0 || seq >= p->next_seq || seq < p->next_seq - S) return DD_ERR_STATE;
@@ -530,7 +690,8 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     DD_TRYCK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
     DD_TRYCK(cudaEventCreateWithFlags(&s.ev_free, cudaEventDisableTiming));
     DD_TRYCK(cudaEventCreateWithFlags(&s.ev_sps, cudaEventDisableTiming));
-    DD_TRY(dalloc(&s.staging, (size_t)p->L * nchans, "staging"));
+    if (!(o.flags & DD_FLAG_DEVICE_INPUT))
+      DD_TRY(dalloc(&s.staging, (size_t)p->L * nchans, "staging"));
     DD_TRY(dalloc(&s.ring1, (size_t)p->C4 * p->R1, "ring"));
     DD_TRYCK(cudaMemset(s.ring1, 0, (size_t)p->C4 * p->R1));
     for (int l = 1; l <= p->levels; ++l) {
@@ -596,6 +757,9 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
 
   cudaPointerAttributes attr;
   DD_CK(cudaPointerGetAttributes(&attr, chunk));
+  if ((p->opts.flags & DD_FLAG_DEVICE_INPUT) && attr.type != cudaMemoryTypeDevice &&
+      attr.type != cudaMemoryTypeManaged)
+    return fail(DD_ERR_ARG, "the plan takes device chunks only (DD_FLAG_DEVICE_INPUT)");
   const uint8_t* src = chunk;
   if (attr.type == cudaMemoryTypeUnregistered && p->pool) {
     // pageable chunk: host threads copy it into the slot's pinned buffer (once the previous
