@@ -347,6 +347,82 @@ def serve_workload(args):
     return 0
 
 
+def batch_workload(args):
+    """48 beams of log-uniform length 2^18-2^21 with 1024 or 4096 channels, DM 0-500: one
+    captured, autotuned batch step against the plain per-chunk loop over the same beams."""
+    import torch
+
+    import paper_2101_00941_gb300 as dd
+    torch.cuda.set_device(0)
+    dd.build()
+    ws = configs.batched_beams()
+    if args.batch_scale > 1:
+        for w in ws:
+            w.nsamp = max(1 << 17, w.nsamp // args.batch_scale // 128 * 128)
+    big = max(w.nsamp * w.nchans for w in ws)
+    pinned = torch.empty(big, dtype=torch.uint8, pin_memory=True)
+    dev = []
+    for w in ws:
+        h = pinned[:w.nsamp * w.nchans].view(w.nsamp, w.nchans)
+        w.generate(pulse_offsets(w), out=h.numpy())
+        dev.append(h.cuda())
+    del pinned
+    L = 1 << 17
+    outs = 0
+    t_build = time.perf_counter()
+    b = dd.Batch([(w.freqs(), w.tsamp, d) for w, d in zip(ws, dev)], ws[0].ranges_array(), L,
+                 ws[0].widths, ws[0].threshold, n_streams=1, graph=True, autotune=True,
+                 cap_per_chunk=1 << 16)
+    t_build = time.perf_counter() - t_build
+    for i in range(len(ws)):
+        outs += b.info(i)[1]
+    tiles = sorted({b.info(i)[2] for i in range(len(ws))})
+    for _ in range(args.warmup):
+        b.run()
+        b.wait()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        b.run()
+        b.wait()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ncand = sum(b.candidates(i, k).size for i in range(len(ws)) for k in range(b.info(i)[0]))
+    b.close()
+    # plain per-chunk loop: each beam alone, one stream, every chunk synchronised
+    torch.cuda.synchronize()
+    e0.record()
+    for w, d in zip(ws, dev):
+        p = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=1,
+                    max_width=max(w.widths), flags=dd.DD_FLAG_DEVICE_INPUT)
+        for k in range(0, w.nsamp, L):
+            p.run(d[k:k + L], min(L, w.nsamp - k))
+            p.search(w.widths, w.threshold)
+            p.candidates()
+        p.close()
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    obs = sum(w.nsamp for w in ws) * 64e-6
+    line = {
+        "metric": METRIC, "value": outs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32",
+        "data": "synthetic",
+        "config": {"workload": f"batch_{len(ws)}beams_1024-4096ch", "beams": len(ws),
+                   "samples": int(sum(w.nsamp for w in ws)), "input_gb":
+                   sum(w.nsamp * w.nchans for w in ws) / 1e9, "graph": True, "autotuned_tiles":
+                   tiles, "plan_and_capture_s": t_build, "candidates": ncand},
+        "real_time_factor": obs / (ms * 1e-3),
+        "plain_loop": {"value": outs / (plain_ms * 1e-3), "ms": plain_ms,
+                       "real_time_factor": obs / (plain_ms * 1e-3)},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main(args):
     import torch
 
@@ -438,7 +514,9 @@ if __name__ == "__main__":
     ap.add_argument("--nsamp", type=int, default=1 << 20,
                     help="samples per beam (a multiple of 2^17; smaller only for profiler captures)")
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the chunks rotate over")
-    ap.add_argument("--workload", choices=["mid", "serve"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "serve", "batch"], default="mid")
+    ap.add_argument("--batch-scale", type=int, default=1,
+                    help="batch: divide every beam's length by this (profiling only)")
     ap.add_argument("--beams", type=int, default=16, help="serve: beams")
     ap.add_argument("--chunks-per-beam", type=int, default=6, help="serve: chunks per beam")
     ap.add_argument("--speedup", type=float, default=8.0,
@@ -447,4 +525,6 @@ if __name__ == "__main__":
     a = ap.parse_args()
     if a.impl == "reference":
         sys.exit(main_reference(a))
-    sys.exit(serve_workload(a) if a.workload == "serve" else main(a))
+    if a.workload == "serve":
+        sys.exit(serve_workload(a))
+    sys.exit(batch_workload(a) if a.workload == "batch" else main(a))
