@@ -116,6 +116,16 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
 int dd_plan_info(dd_plan_t plan, int64_t* overlap, int32_t* ntrials, const int32_t** shifts);
 
 /*
+ * dd_plan_kernel -- which dedispersion kernel range `range` (0-based, plan order) runs on.
+ *   tiled        : 1 = the tiled delay-class kernel, 0 = the per-output kernel (chosen when the
+ *                  range's delay classes or decimation exceed the tiled kernel's table limits,
+ *                  or with DD_FLAG_NAIVE) (may be NULL)
+ *   tile_samples : outputs per time tile of the tiled kernel, 0 for the other (may be NULL)
+ * Errors: DD_ERR_ARG (NULL plan, range out of bounds).
+ */
+int dd_plan_kernel(dd_plan_t plan, int32_t range, int32_t* tiled, int32_t* tile_samples);
+
+/*
  * dd_run -- enqueue the dedispersion of the next time chunk (Sec. 1, Sec. 2.1).
  *   chunk       : time-major uint8 [nsamp][nchans]; a host pointer (pinned memory gives
  *                 asynchronous copies, Sec. 2.1) or a device pointer. Read-only; it must stay

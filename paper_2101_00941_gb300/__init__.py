@@ -28,7 +28,7 @@ DD_FLAG_DEVICE_INPUT = 4
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
 
-EXPORTS = ("dd_plan", "dd_plan_info", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
+EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
            "dd_stats", "dd_sps_static", "dd_serve_create", "dd_serve_add_beam", "dd_serve_submit",
            "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_batch_create",
            "dd_batch_run", "dd_batch_wait", "dd_batch_info", "dd_batch_candidates",
@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         P = ctypes.POINTER
         L.dd_plan.argtypes = [vp, i32, f64, vp, i32, P(dd_opts_t), P(vp)]
         L.dd_plan_info.argtypes = [vp, P(i64), P(i32), P(vp)]
+        L.dd_plan_kernel.argtypes = [vp, i32, P(i32), P(i32)]
         L.dd_run.argtypes = [vp, vp, i64, vp]
         L.dd_series.argtypes = [vp, i32, P(vp), P(i64), P(i64), P(i64)]
         L.sps_run.argtypes = [vp, vp, i32, f32]
@@ -165,6 +166,13 @@ def dd_plan_info(plan: int, nchans: int):
     return O.value, nt.value, np.ctypeslib.as_array(buf).reshape(nt.value, nchans).copy()
 
 
+def dd_plan_kernel(plan: int, range_idx: int):
+    """(1 if range `range_idx` runs on the tiled kernel else 0, its time tile or 0)."""
+    t, tt = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().dd_plan_kernel(plan, int(range_idx), ctypes.byref(t), ctypes.byref(tt)))
+    return t.value, tt.value
+
+
 def dd_run(plan: int, chunk, nsamp: int, cuda_stream: int = 0):
     _check(lib().dd_run(plan, _ptr(chunk), int(nsamp), int(cuda_stream) or None))
 
@@ -228,6 +236,10 @@ class Plan:
         self.h = dd_plan(freqs_mhz, tsamp_s, ranges, chunk_len, **kw)
         self.O, self.ntrials, self.shifts = dd_plan_info(self.h, self.nchans)
         self.seq = -1
+
+    def kernel(self, range_idx):
+        """(tiled, tile samples) of one range; see dd_plan_kernel."""
+        return dd_plan_kernel(self.h, range_idx)
 
     def run(self, chunk, nsamp=None, cuda_stream=0) -> int:
         n = chunk.shape[0] if nsamp is None else nsamp

@@ -139,8 +139,8 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaStream_t used = nullptr;  // stream the current chunk was enqueued on
   uint8_t* staging = nullptr;   // [chunk_len][nchans] host-input landing buffer
-  uint8_t* ring1 = nullptr;     // [C4][R1] channel-major, column 0 = global sample T - H
-  uint16_t* ringd[9] = {};      // level l >= 1 (decimation 2^l): [C4][Rd[l]]
+  uint8_t* ring1 = nullptr;     // [Cp][R1] channel-major, column 0 = global sample T - H
+  uint16_t* ringd[9] = {};      // level l >= 1 (decimation 2^l): [Cp][Rd[l]]
   int32_t* series = nullptr;    // every range, at series_off[r]
   ddk::Moments* mom = nullptr;  // [total trials]
   dd_cand_t* cands = nullptr;   // [max_cands]
@@ -169,14 +169,14 @@ struct RangeKernel {
 
 struct dd_plan_s {
   int device = 0;
-  int32_t C = 0, C4 = 0;
+  int32_t C = 0, Cp = 0;
   double tsamp = 0;
   std::vector<dd_range_t> ranges;
   dd_opts_t opts{};
   std::vector<int32_t> row0;       // first shift-table row of each range
   int32_t total_rows = 0;
   std::vector<int32_t> h_shifts;   // [total_rows][C] (plan_info view)
-  int32_t* d_shifts = nullptr;     // [total_rows][C4]
+  int32_t* d_shifts = nullptr;     // [total_rows][Cp]
   int64_t O = 0, H = 0, L = 0;
   int dmax = 1, levels = 0;
   int64_t R1 = 0;
@@ -184,7 +184,7 @@ struct dd_plan_s {
   std::vector<int64_t> series_off, series_stride;
   int64_t series_elems = 0;
   std::vector<RangeKernel> rk;
-  uint8_t* hist = nullptr;         // [C4][H] device history
+  uint8_t* hist = nullptr;         // [Cp][H] device history
   cudaEvent_t ev_hist = nullptr;
   std::vector<Slot> slots;
   cudaStream_t io = nullptr;
@@ -388,8 +388,8 @@ int plan_autotune(dd_plan_s* p) {
     const int d = p->ranges[r].decimation;
     const bool u16 = d > 1;
     const int l = ilog2(d);
-    std::vector<int32_t> tab((size_t)p->ranges[r].n_trials * p->C4);
-    if (cudaMemcpy(tab.data(), p->d_shifts + (int64_t)p->row0[r] * p->C4,
+    std::vector<int32_t> tab((size_t)p->ranges[r].n_trials * p->Cp);
+    if (cudaMemcpy(tab.data(), p->d_shifts + (int64_t)p->row0[r] * p->Cp,
                    sizeof(int32_t) * tab.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
       rc = fail(DD_ERR_CUDA, "autotune: reading the delay table failed");
       break;
@@ -403,7 +403,7 @@ int plan_autotune(dd_plan_s* p) {
       if (tt == cur.tt) {
         k = cur;
       } else {
-        tp = ddk::tiled_plan(tab.data(), p->ranges[r].n_trials, p->C4, u16, tt);
+        tp = ddk::tiled_plan(tab.data(), p->ranges[r].n_trials, p->Cp, d, tt);
         if (!tp.ok) continue;
         if (dalloc(&k.d_tabs, tp.tab_bytes, "delay-class tables")) {
           rc = DD_ERR_NOMEM;
@@ -430,9 +430,9 @@ int plan_autotune(dd_plan_s* p) {
       A.y = s.series + p->series_off[r];
       A.y_stride = p->series_stride[r];
       A.mom = s.mom + p->row0[r];
-      A.shifts = p->d_shifts + (int64_t)p->row0[r] * p->C4;
+      A.shifts = p->d_shifts + (int64_t)p->row0[r] * p->Cp;
       A.n_trials = p->ranges[r].n_trials;
-      A.c4 = p->C4;
+      A.cpad = p->Cp;
       A.row_slot = k.row_slot;
       A.zcap = k.zcap;
       A.tabs = k.d_tabs;
@@ -541,7 +541,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
   dd_plan_s* p = new dd_plan_s();
   p->device = o.device;
   p->C = nchans;
-  p->C4 = (int32_t)round_up(nchans, 4);
+  p->Cp = (int32_t)round_up(nchans, 8);
   p->tsamp = tsamp_s;
   p->ranges.assign(ranges, ranges + nranges);
   p->opts = o;
@@ -582,7 +582,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
   for (int c = 1; c < nchans; ++c) fref = std::max(fref, freqs_mhz[c]);
   double* d_freqs = nullptr;
   int32_t* d_err = nullptr;
-  DD_TRY(dalloc(&p->d_shifts, sizeof(int32_t) * (size_t)total_rows * p->C4, "delay table"));
+  DD_TRY(dalloc(&p->d_shifts, sizeof(int32_t) * (size_t)total_rows * p->Cp, "delay table"));
   DD_TRY(dalloc(&d_freqs, sizeof(double) * nchans, "frequencies"));
   if (dalloc(&d_err, sizeof(int32_t), "flag")) {
     cudaFree(d_freqs);
@@ -593,11 +593,11 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     cudaError_t e = cudaMemcpy(d_freqs, freqs_mhz, sizeof(double) * nchans, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(int32_t));
     if (e == cudaSuccess)
-      e = ddk::launch_shift_table(d_freqs, nchans, p->C4, fref, tsamp_s, sr.data(), nranges,
+      e = ddk::launch_shift_table(d_freqs, nchans, p->Cp, fref, tsamp_s, sr.data(), nranges,
                                   (int32_t)total_rows, p->d_shifts, d_err, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     int32_t herr = 0;
-    std::vector<int32_t> full((size_t)total_rows * p->C4);
+    std::vector<int32_t> full((size_t)total_rows * p->Cp);
     if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof herr, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
       e = cudaMemcpy(full.data(), p->d_shifts, sizeof(int32_t) * full.size(),
@@ -615,7 +615,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     }
     p->h_shifts.resize((size_t)total_rows * nchans);
     for (int64_t rr = 0; rr < total_rows; ++rr)
-      std::memcpy(&p->h_shifts[rr * nchans], &full[rr * p->C4], sizeof(int32_t) * nchans);
+      std::memcpy(&p->h_shifts[rr * nchans], &full[rr * p->Cp], sizeof(int32_t) * nchans);
     // overlap O = d_max * ceil(max_r(d_r * max s_r) / d_max)
     int64_t need = 0;
     for (int r = 0; r < nranges; ++r) {
@@ -631,8 +631,9 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
         const bool u16 = ranges[r].decimation > 1;
         for (int choice = 0; choice < 2; ++choice) {
           const int tt = ddk::tiled_tile_samples(u16, choice);
-          ddk::TiledPlan tp = ddk::tiled_plan(&full[(size_t)p->row0[r] * p->C4],
-                                              ranges[r].n_trials, p->C4, u16, tt);
+          ddk::TiledPlan tp = ddk::tiled_plan(&full[(size_t)p->row0[r] * p->Cp],
+                                              ranges[r].n_trials, p->Cp,
+                                              ranges[r].decimation, tt);
           if (!tp.ok) continue;
           RangeKernel& k = p->rk[r];
           if (dalloc(&k.d_tabs, tp.tab_bytes, "delay-class tables")) {
@@ -674,8 +675,8 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
   p->series_elems = off;
 
   // ---- buffers (all allocation happens here)
-  DD_TRY(dalloc(&p->hist, (size_t)p->C4 * std::max<int64_t>(p->H, 1), "history"));
-  DD_TRYCK(cudaMemset(p->hist, 0, (size_t)p->C4 * std::max<int64_t>(p->H, 1)));
+  DD_TRY(dalloc(&p->hist, (size_t)p->Cp * std::max<int64_t>(p->H, 1), "history"));
+  DD_TRYCK(cudaMemset(p->hist, 0, (size_t)p->Cp * std::max<int64_t>(p->H, 1)));
   DD_TRYCK(cudaEventCreateWithFlags(&p->ev_hist, cudaEventDisableTiming));
   DD_TRYCK(cudaStreamCreateWithFlags(&p->io, cudaStreamNonBlocking));
   DD_TRYCK(cudaEventCreateWithFlags(&p->ev_io, cudaEventDisableTiming));
@@ -692,11 +693,11 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     DD_TRYCK(cudaEventCreateWithFlags(&s.ev_sps, cudaEventDisableTiming));
     if (!(o.flags & DD_FLAG_DEVICE_INPUT))
       DD_TRY(dalloc(&s.staging, (size_t)p->L * nchans, "staging"));
-    DD_TRY(dalloc(&s.ring1, (size_t)p->C4 * p->R1, "ring"));
-    DD_TRYCK(cudaMemset(s.ring1, 0, (size_t)p->C4 * p->R1));
+    DD_TRY(dalloc(&s.ring1, (size_t)p->Cp * p->R1, "ring"));
+    DD_TRYCK(cudaMemset(s.ring1, 0, (size_t)p->Cp * p->R1));
     for (int l = 1; l <= p->levels; ++l) {
-      DD_TRY(dalloc(&s.ringd[l], sizeof(uint16_t) * (size_t)p->C4 * p->Rd[l], "decimated ring"));
-      DD_TRYCK(cudaMemset(s.ringd[l], 0, sizeof(uint16_t) * (size_t)p->C4 * p->Rd[l]));
+      DD_TRY(dalloc(&s.ringd[l], sizeof(uint16_t) * (size_t)p->Cp * p->Rd[l], "decimated ring"));
+      DD_TRYCK(cudaMemset(s.ringd[l], 0, sizeof(uint16_t) * (size_t)p->Cp * p->Rd[l]));
     }
     DD_TRY(dalloc(&s.series, sizeof(int32_t) * (size_t)p->series_elems, "series"));
     DD_TRY(dalloc(&s.mom, sizeof(ddk::Moments) * (size_t)total_rows, "moments"));
@@ -741,6 +742,15 @@ int dd_plan_info(dd_plan_t p, int64_t* overlap, int32_t* ntrials, const int32_t*
   return DD_OK;
 }
 
+int dd_plan_kernel(dd_plan_t p, int32_t range, int32_t* tiled, int32_t* tile_samples) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (range < 0 || range >= (int32_t)p->rk.size())
+    return fail(DD_ERR_ARG, "range %d out of bounds", (int)range);
+  if (tiled) *tiled = p->rk[range].tiled ? 1 : 0;
+  if (tile_samples) *tile_samples = p->rk[range].tiled ? p->rk[range].tt : 0;
+  return DD_OK;
+}
+
 int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) {
   if (!p) return fail(DD_ERR_ARG, "plan is NULL");
   if (!chunk) return fail(DD_ERR_ARG, "chunk is NULL");
@@ -776,11 +786,11 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
   }
   const int64_t H = p->H;
   if (seq > 0 && H > 0)
-    DD_CK(cudaMemcpy2DAsync(s.ring1, p->R1, p->hist, H, H, p->C4, cudaMemcpyDeviceToDevice, st));
+    DD_CK(cudaMemcpy2DAsync(s.ring1, p->R1, p->hist, H, H, p->Cp, cudaMemcpyDeviceToDevice, st));
   DD_CK(ddk::launch_corner_turn(src, nsamp, p->C, s.ring1, p->R1, H, st));
   p->launches += 1;
   if (H > 0) {
-    DD_CK(cudaMemcpy2DAsync(p->hist, H, s.ring1 + nsamp, p->R1, H, p->C4,
+    DD_CK(cudaMemcpy2DAsync(p->hist, H, s.ring1 + nsamp, p->R1, H, p->Cp,
                             cudaMemcpyDeviceToDevice, st));
     DD_CK(cudaEventRecord(p->ev_hist, st));
   }
@@ -788,7 +798,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
   for (int l = 1; l <= p->levels; ++l) {
     const void* in = (l == 1) ? (const void*)s.ring1 : (const void*)s.ringd[l - 1];
     const int64_t in_stride = (l == 1) ? p->R1 : p->Rd[l - 1];
-    DD_CK(ddk::launch_decimate(in, l > 1, in_stride, s.ringd[l], p->Rd[l], p->C4,
+    DD_CK(ddk::launch_decimate(in, l > 1, in_stride, s.ringd[l], p->Rd[l], p->Cp,
                                (H + nsamp) >> l, st));
     p->launches += 1;
   }
@@ -806,7 +816,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
     R.y = s.series + p->series_off[r];
     R.y_stride = p->series_stride[r];
     R.mom = s.mom + p->row0[r];
-    R.shifts = p->d_shifts + (int64_t)p->row0[r] * p->C4;
+    R.shifts = p->d_shifts + (int64_t)p->row0[r] * p->Cp;
     R.n_trials = p->ranges[r].n_trials;
     R.is_u16 = l > 0;
     if (R.nout <= 0) continue;
@@ -825,7 +835,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       A.mom = R.mom;
       A.shifts = R.shifts;
       A.n_trials = R.n_trials;
-      A.c4 = p->C4;
+      A.cpad = p->Cp;
       A.row_slot = K.row_slot;
       A.zcap = K.zcap;
       A.tabs = K.d_tabs;
@@ -833,7 +843,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, st));
       p->launches += 1;
     } else {
-      DD_CK(ddk::launch_dedisp_naive(R, p->C4, st));
+      DD_CK(ddk::launch_dedisp_naive(R, p->Cp, st));
     }
     rc = timing_end(p, st, ts);
     if (rc) return rc;

@@ -2,25 +2,26 @@
 // plain definition y[i][j] = sum_c x_d[c][j + s[i][c]], computed exactly in integers).
 //
 // One CTA (16 warps) owns a tile of kTileTrials consecutive DM trials x TT output samples of one
-// range and walks the channels in stages of kNG groups of four channels.
+// range and walks the channels in stages of kNG groups of eight channels.
 //
-//   * Delay classes. For a 4-channel group the tile's trials fall into a few classes by the
-//     relative delays (r0, r1, r2, r3) of the four channels. A class shares one "pattern word"
-//     sequence
-//        Z_p[u] = x[c0][a + u + r0] | x[c1][a + u + r1] << 8 | x[c2][..] << 16 | x[c3][..] << 24
-//     that each of its trials reads at its own base offset. The classes depend on the delay
+//   * Delay classes. For an 8-channel group the tile's trials fall into a few classes by the
+//     relative delays (r0..r7) of the eight channels. A class shares one "pattern word" sequence
+//        Z_p[u] = (x[c0][a+u+r0] + .. + x[c3][a+u+r3]) | (x[c4][a+u+r4] + .. + x[c7][..]) << 16
+//     -- two 16-bit lanes, each the exact sum of four channels (4 x 255 x d < 2^16 for d <= 64)
+//     -- that each of its trials reads at its own base offset. The classes depend on the delay
 //     table only, so the plan computes them once (tiled_plan, below) as one fixed-size table per
 //     (trial tile, stage); the kernel never searches for them.
 //   * TMA (cp.async.bulk) brings each stage's 16 channel rows and its class table into shared
 //     memory kNStage stages ahead; completion is tracked by mbarriers with bounded waits.
-//   * The main loop adds one pattern word per (trial, sample): DP4A for uint8 data, two DP2A
-//     for uint16 (decimated) data -- one shared-memory load per four channel-adds.
+//   * The main loop adds one pattern word per (trial, sample) with one DP2A: one 32-bit
+//     shared-memory load per eight channel-adds, for uint8 and uint16 (decimated) data alike.
 //
 // Software pipeline, one __syncthreads per stage s:
 //     TMA for stage s+kNStage-1 | build the words of stage s+1 | accumulate stage s
-// Words are built four (uint8) or two (uint16) at a time from aligned 32-bit loads, funnel
-// shifts and a byte transpose. Exact moments (S1, 128-bit S2) of every series are added in the
-// epilogue with integer atomics, so the search needs no second statistics pass.
+// Words are built from aligned 32-bit loads and funnel shifts; the four-channel sums are formed
+// in SWAR lanes (bytes split into 16-bit lanes for uint8 data). Exact moments (S1, 128-bit S2)
+// of every series are added in the epilogue with integer atomics, so the search needs no second
+// statistics pass.
 #include <algorithm>
 #include <cstring>
 
@@ -34,16 +35,17 @@ constexpr int kTileTrials = 64;
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTPW = kTileTrials / kWarps;  // trials per warp
-constexpr int kNG = 4;                      // 4-channel groups per stage
-constexpr int kRows = 4 * kNG;              // channel rows per stage
+constexpr int kG = 8;                       // channels per group (one pattern word)
+constexpr int kNG = 2;                      // groups per stage
+constexpr int kRows = kG * kNG;             // channel rows per stage
 constexpr int kNStage = 4;                  // staging buffers (rows + class table)
-constexpr int kMaxCls = 8;                  // classes per group
-constexpr int kMaxItems = 32;               // build items (64 units of one class) per group
+constexpr int kMaxCls = 16;                 // classes per group
+constexpr int kMaxItems = 64;               // build items (64 units of one class) per group
 
 // One delay class: its channels' first staged sample relative to the tile's first trial
 // (rel), and its words in the stage's pattern-word region.
 struct ClsEntry {
-  int16_t rel[4];
+  int16_t rel[kG];
   int16_t zoff;  // first word (multiple of 4)
   int16_t zlen;  // words (multiple of 4)
   int32_t pad;
@@ -146,12 +148,12 @@ __device__ void issue_stage(const TiledArgs& a, int stage, int nstages, T* raw_b
                             int trial0, int ntr, int64_t j0, int lane) {
   constexpr int A = 16 / (int)sizeof(T);  // elements per 16 bytes
   const int c = stage * kRows + lane;
-  const bool mine = lane < kRows && c < a.c4;
+  const bool mine = lane < kRows && c < a.cpad;
   int64_t a0 = 0;
   uint32_t nb = 0;
   if (mine) {
-    const int32_t smin = __ldg(a.shifts + (int64_t)trial0 * a.c4 + c);
-    const int32_t smax = __ldg(a.shifts + (int64_t)(trial0 + ntr - 1) * a.c4 + c);
+    const int32_t smin = __ldg(a.shifts + (int64_t)trial0 * a.cpad + c);
+    const int32_t smax = __ldg(a.shifts + (int64_t)(trial0 + ntr - 1) * a.cpad + c);
     const int64_t start = a.m0 + j0 + smin;
     a0 = start & ~(int64_t)(A - 1);
     const int64_t end = a.m0 + j0 + smax + TT;
@@ -179,122 +181,126 @@ __device__ void issue_stage(const TiledArgs& a, int stage, int nstages, T* raw_b
 template <typename T>
 struct Word;
 
-// uint8 data: a unit is four consecutive pattern words. Because a unit starts on a multiple of
-// four samples, each channel row is read at a fixed byte phase per class: the row pointer and
-// the funnel-shift amount are set once per item.
+// Row access shared by both data types: for each of the group's eight channels, the row word
+// holding the class's sample 0 and the bit phase of that sample in it. A build unit starts on a
+// multiple of the samples per row word, so the phase is fixed per class: set once per item.
+struct RowItem {
+  const uint32_t* rp[kG];
+  uint32_t sh[kG];
+};
+
+template <int EPW>  // elements per 32-bit row word
+__device__ __forceinline__ RowItem row_item(const uint32_t* rows, int row_words, int g,
+                                            const int (&col)[kG]) {
+  RowItem it;
+#pragma unroll
+  for (int k = 0; k < kG; ++k) {
+    it.rp[k] = rows + (size_t)(kG * g + k) * row_words + col[k] / EPW;
+    it.sh[k] = (uint32_t)(col[k] % EPW) * (32u / EPW);
+  }
+  return it;
+}
+
+// uint8 data: a lane builds 8 consecutive pattern words (two units of 4) from three row words
+// per channel; bytes are split into even/odd 16-bit lanes so that four channels add without
+// carries, then the two four-channel sums of each sample are paired into its word.
 template <>
 struct Word<uint8_t> {
-  using Z = uint32_t;
-  static constexpr int kUnit = 4;
-  struct Item {
-    const uint32_t* rp[4];  // row word holding the class's sample 0 of channel k
-    uint32_t sh[4];         // bit phase of that sample in the word
-  };
-  static __device__ __forceinline__ Item item(const uint8_t* rawb, int row_slot, int g,
-                                              const int (&col)[4]) {
-    Item it;
+  static constexpr int kUnit = 4;  // pattern words per unit
+  static constexpr int kEPW = 4;
+  static __device__ __forceinline__ void sums(const uint32_t (&v)[kG], uint4& out) {
+    uint32_t elo = 0, olo = 0, ehi = 0, ohi = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      it.rp[k] = reinterpret_cast<const uint32_t*>(rawb + (size_t)(4 * g + k) * row_slot) +
-                 (col[k] >> 2);
-      it.sh[k] = (uint32_t)(col[k] & 3) * 8u;
+      elo += v[k] & 0x00FF00FFu;             // samples 0, 2
+      olo += __byte_perm(v[k], 0, 0x4341);   // samples 1, 3
+      ehi += v[k + 4] & 0x00FF00FFu;
+      ohi += __byte_perm(v[k + 4], 0, 0x4341);
     }
-    return it;
+    out.x = __byte_perm(elo, ehi, 0x5410);  // sample 0: (ch0-3 sum) | (ch4-7 sum) << 16
+    out.y = __byte_perm(olo, ohi, 0x5410);  // sample 1
+    out.z = __byte_perm(elo, ehi, 0x7632);  // sample 2
+    out.w = __byte_perm(olo, ohi, 0x7632);  // sample 3
   }
-  static __device__ __forceinline__ uint4 transpose(const uint32_t (&v)[4]) {
-    // 4x4 byte transpose: word t gets byte t of every channel
-    const uint32_t a0 = __byte_perm(v[0], v[1], 0x5140), a1 = __byte_perm(v[0], v[1], 0x7362);
-    const uint32_t a2 = __byte_perm(v[2], v[3], 0x5140), a3 = __byte_perm(v[2], v[3], 0x7362);
-    uint4 o;
-    o.x = __byte_perm(a0, a2, 0x5410);
-    o.y = __byte_perm(a0, a2, 0x7632);
-    o.z = __byte_perm(a1, a3, 0x5410);
-    o.w = __byte_perm(a1, a3, 0x7632);
-    return o;
-  }
-  // units 2p and 2p + 1 = pattern words 8p .. 8p + 7 (three row words per channel)
-  static __device__ __forceinline__ void build2(const Item& it, int p, bool second, Z* dst) {
-    uint32_t v0[4], v1[4];
+  // units 2p and 2p + 1 = pattern words 8p .. 8p + 7
+  static __device__ __forceinline__ void build2(const RowItem& it, int p, bool second,
+                                                uint32_t* dst) {
+    uint32_t a[kG], b[kG];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kG; ++k) {
       const uint32_t w0 = it.rp[k][2 * p], w1 = it.rp[k][2 * p + 1], w2 = it.rp[k][2 * p + 2];
-      v0[k] = __funnelshift_r(w0, w1, it.sh[k]);
-      v1[k] = __funnelshift_r(w1, w2, it.sh[k]);
+      a[k] = __funnelshift_r(w0, w1, it.sh[k]);
+      b[k] = __funnelshift_r(w1, w2, it.sh[k]);
     }
-    reinterpret_cast<uint4*>(dst)[2 * p] = transpose(v0);
-    if (second) reinterpret_cast<uint4*>(dst)[2 * p + 1] = transpose(v1);
-  }
-  static __device__ __forceinline__ uint32_t dot(uint32_t z, uint32_t acc) {
-    return __dp4a(z, 0x01010101u, acc);
+    uint4 o;
+    sums(a, o);
+    reinterpret_cast<uint4*>(dst)[2 * p] = o;
+    if (second) {
+      sums(b, o);
+      reinterpret_cast<uint4*>(dst)[2 * p + 1] = o;
+    }
   }
 };
 
-// uint16 data: a pattern word is 4 x 16 bits (uint2); a unit is two consecutive words.
+// uint16 data: a lane builds 4 consecutive pattern words (two units of 2): 16-bit lanes add
+// four channels without carries (4 x 255 x d < 2^16).
 template <>
 struct Word<uint16_t> {
-  using Z = uint2;
   static constexpr int kUnit = 2;
-  struct Item {
-    const uint32_t* rp[4];
-    uint32_t sh[4];
-  };
-  static __device__ __forceinline__ Item item(const uint16_t* rawb, int row_slot, int g,
-                                              const int (&col)[4]) {
-    Item it;
+  static constexpr int kEPW = 2;
+  // units 2p and 2p + 1 = pattern words 4p .. 4p + 3
+  static __device__ __forceinline__ void build2(const RowItem& it, int p, bool second,
+                                                uint32_t* dst) {
+    uint32_t alo = 0, ahi = 0, blo = 0, bhi = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      it.rp[k] = reinterpret_cast<const uint32_t*>(rawb + (size_t)(4 * g + k) * row_slot) +
-                 (col[k] >> 1);
-      it.sh[k] = (uint32_t)(col[k] & 1) * 16u;
-    }
-    return it;
-  }
-  static __device__ __forceinline__ uint4 pack(const uint32_t (&v)[4]) {
-    uint4 o;
-    o.x = __byte_perm(v[0], v[1], 0x5410);  // word 2m:   channels 0,1
-    o.y = __byte_perm(v[2], v[3], 0x5410);  //            channels 2,3
-    o.z = __byte_perm(v[0], v[1], 0x7632);  // word 2m+1: channels 0,1
-    o.w = __byte_perm(v[2], v[3], 0x7632);  //            channels 2,3
-    return o;
-  }
-  // units 2p and 2p + 1 = pattern words 4p .. 4p + 3 (three row words per channel)
-  static __device__ __forceinline__ void build2(const Item& it, int p, bool second, Z* dst) {
-    uint32_t v0[4], v1[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kG; ++k) {
       const uint32_t w0 = it.rp[k][2 * p], w1 = it.rp[k][2 * p + 1], w2 = it.rp[k][2 * p + 2];
-      v0[k] = __funnelshift_r(w0, w1, it.sh[k]);
-      v1[k] = __funnelshift_r(w1, w2, it.sh[k]);
+      const uint32_t a = __funnelshift_r(w0, w1, it.sh[k]);  // samples 0, 1
+      const uint32_t b = __funnelshift_r(w1, w2, it.sh[k]);  // samples 2, 3
+      if (k < 4) {
+        alo += a;
+        blo += b;
+      } else {
+        ahi += a;
+        bhi += b;
+      }
     }
-    reinterpret_cast<uint4*>(dst)[2 * p] = pack(v0);
-    if (second) reinterpret_cast<uint4*>(dst)[2 * p + 1] = pack(v1);
-  }
-  static __device__ __forceinline__ uint32_t dot(uint2 z, uint32_t acc) {
-    return __dp2a_lo(z.y, 0x0101u, __dp2a_lo(z.x, 0x0101u, acc));
+    uint2 o;
+    o.x = __byte_perm(alo, ahi, 0x5410);  // sample 0
+    o.y = __byte_perm(alo, ahi, 0x7632);  // sample 1
+    reinterpret_cast<uint2*>(dst)[2 * p] = o;
+    if (second) {
+      o.x = __byte_perm(blo, bhi, 0x5410);  // sample 2
+      o.y = __byte_perm(blo, bhi, 0x7632);  // sample 3
+      reinterpret_cast<uint2*>(dst)[2 * p + 1] = o;
+    }
   }
 };
+
+__device__ __forceinline__ uint32_t dot(uint32_t z, uint32_t acc) {
+  return __dp2a_lo(z, 0x0101u, acc);  // acc + (ch0-3 sum) + (ch4-7 sum)
+}
 
 // Build every pattern word of one stage. The plan cut the work into items of 64 units of one
 // class; warp w takes items w, w + kWarps, ... and each lane builds two adjacent units.
 template <typename T>
 __device__ __forceinline__ void build_stage(const StageTab& tb, int ng, const T* rawb,
-                                            const int32_t* phase, int row_slot,
-                                            typename Word<T>::Z* Zs, int warp, int lane) {
+                                            const int32_t* phase, int row_slot, uint32_t* Zs,
+                                            int warp, int lane) {
   constexpr int U = Word<T>::kUnit;
   const int n0 = tb.g[0].nitem;
   const int n1 = n0 + (ng > 1 ? tb.g[1].nitem : 0);
-  const int n2 = n1 + (ng > 2 ? tb.g[2].nitem : 0);
-  const int n3 = n2 + (ng > 3 ? tb.g[3].nitem : 0);
-  for (int k = warp; k < n3; k += kWarps) {
-    const int gi = (k >= n0) + (k >= n1) + (k >= n2);
-    const int kb = gi == 0 ? 0 : gi == 1 ? n0 : gi == 2 ? n1 : n2;
+  const uint32_t* rows = reinterpret_cast<const uint32_t*>(rawb);
+  const int row_words = row_slot * (int)sizeof(T) / 4;
+  for (int k = warp; k < n1; k += kWarps) {
+    const int gi = k >= n0 ? 1 : 0;
     const GroupTab& gt = tb.g[gi];
-    const uint32_t itw = gt.item[k - kb];
-    const ClsEntry e = gt.cls[itw >> 8];
-    int col[4];
+    const uint32_t itw = gt.item[k - (gi ? n0 : 0)];
+    const ClsEntry& e = gt.cls[itw >> 8];
+    int col[kG];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) col[q] = e.rel[q] + phase[4 * gi + q];
-    const typename Word<T>::Item it = Word<T>::item(rawb, row_slot, gi, col);
+    for (int q = 0; q < kG; ++q) col[q] = e.rel[q] + phase[kG * gi + q];
+    const RowItem it = row_item<Word<T>::kEPW>(rows, row_words, gi, col);
     const int pu = (int)(itw & 255) * 32 + lane;  // unit pair: units 2pu, 2pu + 1
     if (2 * pu * U < e.zlen) Word<T>::build2(it, pu, (2 * pu + 1) * U < e.zlen, Zs + e.zoff);
   }
@@ -302,12 +308,11 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, int ng, const T*
 
 template <typename T, int TT>
 __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a) {
-  using ZT = typename Word<T>::Z;
   constexpr int KT = TT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout SL = smem_layout(sizeof(T), sizeof(ZT), a.row_slot, a.zcap);
+  const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap);
   T* raw = reinterpret_cast<T*>(smem + SL.raw);
-  ZT* Zbuf = reinterpret_cast<ZT*>(smem + SL.z);
+  uint32_t* Zbuf = reinterpret_cast<uint32_t*>(smem + SL.z);
   StageTab* tab = reinterpret_cast<StageTab*>(smem + SL.tab);
   int32_t* phase = reinterpret_cast<int32_t*>(smem + SL.phase);
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + SL.mbar);
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
   const int trial0 = blockIdx.x * kTileTrials;
   const int ntr = min(kTileTrials, a.n_trials - trial0);
   const int64_t j0 = (int64_t)blockIdx.y * TT;
-  const int ngroups = a.c4 / 4;
+  const int ngroups = a.cpad / kG;
   const int nstages = (ngroups + kNG - 1) / kNG;
   const size_t stage_elems = (size_t)kRows * a.row_slot;
 
@@ -370,17 +375,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
     // (3) accumulate stage s
     {
       const StageTab& tc = tab[s % kNStage];
-      const ZT* Zs = Zbuf + (size_t)(s & 1) * a.zcap + lane;
+      const uint32_t* Zs = Zbuf + (size_t)(s & 1) * a.zcap + lane;
 #pragma unroll
       for (int g = 0; g < kNG; ++g) {
         if (g < ng) {  // uniform; only the last stage may hold fewer groups
-          const ZT* zp[kTPW];
+          const uint32_t* zp[kTPW];
 #pragma unroll
           for (int q = 0; q < kTPW; ++q) zp[q] = Zs + tc.g[g].zstart[warp + kWarps * q];
 #pragma unroll
           for (int k = 0; k < KT; ++k)
 #pragma unroll
-            for (int q = 0; q < kTPW; ++q) acc[q][k] = Word<T>::dot(zp[q][32 * k], acc[q][k]);
+            for (int q = 0; q < kTPW; ++q) acc[q][k] = dot(zp[q][32 * k], acc[q][k]);
         }
       }
     }
@@ -440,8 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
 
 template <typename T, int TT>
 cudaError_t launch_tiled_t(const TiledArgs& a, cudaStream_t st) {
-  using ZT = typename Word<T>::Z;
-  const SmemLayout SL = smem_layout(sizeof(T), sizeof(ZT), a.row_slot, a.zcap);
+  const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap);
   dim3 grid((unsigned)((a.n_trials + kTileTrials - 1) / kTileTrials),
             (unsigned)((a.nout + TT - 1) / TT));
   k_dedisp_tiled<T, TT><<<grid, kThreads, SL.total, st>>>(a);
@@ -472,22 +476,27 @@ int tiled_tile_samples(int is_u16, int choice) {
 
 // Host: delay classes of every (trial tile, stage) of one range, as the kernel reads them.
 // Classes are numbered in order of their first trial; a class's words start at a multiple of 4
-// within the stage, groups one after another.
-TiledPlan tiled_plan(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
+// within the stage, groups one after another. Fails (ok = false) where the kernel's limits do
+// not hold: a 16-bit lane sums four channels of values up to 255 x decimation, so decimation
+// must stay at or below 64; delays must be monotone in the trial within a channel; classes,
+// items and the staged rows must fit their fixed-size tables and shared memory.
+TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int tt) {
   TiledPlan P;
   P.ok = false;
+  const bool u16 = decimation > 1;
+  if (decimation < 1 || 4 * 255 * decimation > 65535 || cpad % kG) return P;
   const int D = kTileTrials, NG = kNG, U = u16 ? 2 : 4;
-  const int ngroups = c4 / 4, nstages = (ngroups + NG - 1) / NG;
+  const int ngroups = cpad / kG, nstages = (ngroups + NG - 1) / NG;
   const int ntiles = (ntr + D - 1) / D;
   int64_t spread = 0, zcap = 0;
   std::vector<StageTab> out((size_t)ntiles * nstages);
   for (int ti = 0; ti < ntiles; ++ti) {
     const int t0 = ti * D, n = std::min(D, ntr - t0);
-    for (int c = 0; c < c4; ++c) {
+    for (int c = 0; c < cpad; ++c) {
       for (int i = 1; i < n; ++i)
-        if (tab[(int64_t)(t0 + i) * c4 + c] < tab[(int64_t)(t0 + i - 1) * c4 + c]) return P;
-      spread = std::max<int64_t>(spread, tab[(int64_t)(t0 + n - 1) * c4 + c] -
-                                             tab[(int64_t)t0 * c4 + c]);
+        if (tab[(int64_t)(t0 + i) * cpad + c] < tab[(int64_t)(t0 + i - 1) * cpad + c]) return P;
+      spread = std::max<int64_t>(spread, tab[(int64_t)(t0 + n - 1) * cpad + c] -
+                                             tab[(int64_t)t0 * cpad + c]);
     }
     for (int s = 0; s < nstages; ++s) {
       StageTab& st = out[(size_t)ti * nstages + s];
@@ -496,24 +505,25 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
       for (int gl = 0; gl < NG && s * NG + gl < ngroups; ++gl) {
         const int g = s * NG + gl;
         GroupTab& gt = st.g[gl];
-        const int32_t* first = tab + (int64_t)t0 * c4 + 4 * g;
+        const int32_t* first = tab + (int64_t)t0 * cpad + kG * g;
         int b[kTileTrials], cls_of[kTileTrials];
-        uint64_t ckey[kTileTrials];
-        int cmin[kTileTrials], cmax[kTileTrials];
+        int32_t ckey[kMaxCls][kG];
+        int cmin[kMaxCls], cmax[kMaxCls];
         int ncls = 0;
         for (int i = 0; i < n; ++i) {
-          const int32_t* sv = tab + (int64_t)(t0 + i) * c4 + 4 * g;
-          b[i] = std::min(std::min(sv[0], sv[1]), std::min(sv[2], sv[3]));
-          uint64_t kk = 0;
-          for (int q = 0; q < 4; ++q) {
+          const int32_t* sv = tab + (int64_t)(t0 + i) * cpad + kG * g;
+          b[i] = *std::min_element(sv, sv + kG);
+          int32_t key[kG];
+          for (int q = 0; q < kG; ++q) {
             const int64_t r = (int64_t)sv[q] - b[i];
             if (r > 32767) return P;
-            kk |= (uint64_t)r << (16 * q);
+            key[q] = (int32_t)r;
           }
           int p = 0;
-          while (p < ncls && ckey[p] != kk) ++p;
+          while (p < ncls && !std::equal(key, key + kG, ckey[p])) ++p;
           if (p == ncls) {
-            ckey[ncls] = kk;
+            if (ncls == kMaxCls) return P;
+            std::copy(key, key + kG, ckey[ncls]);
             cmin[ncls] = cmax[ncls] = b[i];
             ++ncls;
           } else {
@@ -522,21 +532,20 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
           }
           cls_of[i] = p;
         }
-        if (ncls > kMaxCls) return P;
         int nitem = 0;
-        int zoff[kTileTrials];
+        int zoff[kMaxCls];
         for (int p = 0; p < ncls; ++p) {
           const int zlen = (tt + cmax[p] - cmin[p] + 3) & ~3;
           zoff[p] = words;
           ClsEntry& e = gt.cls[p];
-          for (int q = 0; q < 4; ++q) {
-            const int64_t rel = (int64_t)cmin[p] + (int64_t)((ckey[p] >> (16 * q)) & 0xFFFF) -
-                                first[q];
+          for (int q = 0; q < kG; ++q) {
+            const int64_t rel = (int64_t)cmin[p] + ckey[p][q] - first[q];
             if (rel < 0 || rel > 32767) return P;
             e.rel[q] = (int16_t)rel;
           }
           e.zoff = (int16_t)words;
           e.zlen = (int16_t)zlen;
+          // one item = 32 lanes x 2 units
           const int nseg = (zlen / U + 63) / 64;
           for (int q = 0; q < nseg; ++q) {
             if (nitem >= kMaxItems) return P;
@@ -560,7 +569,7 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int c4, bool u16, int tt) {
   // elements the word-wise build may read past the last word it uses
   P.row_slot = (int)(((tt + spread + 2 * A + 16) + A - 1) / A * A);
   P.zcap = (int)((std::max<int64_t>(zcap, 4) + 3) / 4 * 4);
-  P.smem = smem_layout(u16 ? 2 : 1, u16 ? 8 : 4, P.row_slot, P.zcap).total;
+  P.smem = smem_layout(u16 ? 2 : 1, 4, P.row_slot, P.zcap).total;
   P.tab_bytes = out.size() * sizeof(StageTab);
   P.tabs.resize(P.tab_bytes);
   std::memcpy(P.tabs.data(), out.data(), P.tab_bytes);

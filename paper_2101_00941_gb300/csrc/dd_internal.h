@@ -55,30 +55,30 @@ struct DedispTile {
 
 // Per-range geometry of one chunk for the tiled dedispersion kernel.
 struct DedispRange {
-  const void* xd;          // decimated ring: uint8 (d == 1) or uint16 [C4][xd_stride]
+  const void* xd;          // decimated ring: uint8 (d == 1) or uint16 [Cp][xd_stride]
   int64_t xd_stride;       // elements
   int64_t m0;              // ring column of window sample 0
   int64_t nout;            // window length
   int32_t* y;              // [n_trials][y_stride]
   int64_t y_stride;
   Moments* mom;            // [n_trials]
-  const int32_t* shifts;   // [n_trials][C4]
+  const int32_t* shifts;   // [n_trials][Cp]
   int32_t n_trials;
   int32_t is_u16;
 };
 
 // Arguments of the tiled dedispersion kernel (dd_dedisp.cu), one launch per range.
 struct TiledArgs {
-  const void* xd;          // decimated ring, uint8 (d == 1) or uint16, [C4][xd_stride]
+  const void* xd;          // decimated ring, uint8 (d == 1) or uint16, [Cp][xd_stride]
   int64_t xd_stride;       // elements
   int64_t m0;              // ring column of window sample 0
   int64_t nout;            // window length
   int32_t* y;              // [n_trials][y_stride]
   int64_t y_stride;
   Moments* mom;            // [n_trials], zeroed before the launch
-  const int32_t* shifts;   // [n_trials][C4], non-decreasing in the trial index
+  const int32_t* shifts;   // [n_trials][Cp], non-decreasing in the trial index
   int32_t n_trials;
-  int32_t c4;
+  int32_t cpad;
   int32_t row_slot;        // elements per staged channel row
   int32_t zcap;            // pattern words per stage
   const uint8_t* tabs;     // delay-class tables of the range, one per (trial tile, stage)
@@ -98,7 +98,7 @@ struct TiledPlan {
 };
 
 int tiled_tile_samples(int is_u16, int choice);
-TiledPlan tiled_plan(const int32_t* shifts, int ntr, int c4, bool u16, int tt);
+TiledPlan tiled_plan(const int32_t* shifts, int ntr, int cpad, int decimation, int tt);
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st);
 
@@ -122,15 +122,15 @@ int plan_autotune(dd_plan_s* plan);
 int range_tile(dd_plan_s* plan, int r);
 
 // ---- launchers (dd_kernels.cu); each returns the cudaGetLastError() of its launch
-cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t c4, double fref,
+cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t cpad, double fref,
                                double tsamp, const ShiftRange* ranges, int32_t nranges,
                                int32_t total_rows, int32_t* shifts, int32_t* err,
                                cudaStream_t st);
 cudaError_t launch_corner_turn(const uint8_t* in, int64_t n, int32_t nchans, uint8_t* ring,
                                int64_t ring_stride, int64_t col0, cudaStream_t st);
 cudaError_t launch_decimate(const void* in, int in_is_u16, int64_t in_stride, uint16_t* out,
-                            int64_t out_stride, int32_t c4, int64_t n_out, cudaStream_t st);
-cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t c4, cudaStream_t st);
+                            int64_t out_stride, int32_t cpad, int64_t n_out, cudaStream_t st);
+cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t cpad, cudaStream_t st);
 cudaError_t launch_moments(const int32_t* y, int32_t ntr, int64_t n, int64_t stride, Moments* mom,
                            cudaStream_t st);
 cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st);

@@ -17,25 +17,28 @@ namespace ddk {
 
 __constant__ ShiftRange c_ranges[kMaxRanges];
 
-__global__ void k_shift_table(const double* __restrict__ freqs, int32_t nchans, int32_t c4,
+__global__ void k_shift_table(const double* __restrict__ freqs, int32_t nchans, int32_t cpad,
                               double fref, double tsamp, int32_t nranges, int32_t total_rows,
                               int32_t* __restrict__ shifts, int32_t* __restrict__ err) {
-  const int64_t total = (int64_t)total_rows * c4;
+  const int64_t total = (int64_t)total_rows * cpad;
   // k_DM = 4.148808e3 s MHz^2 pc^-1 cm^3 (textbook cold-plasma constant).
   const double kdm = 4.148808e3;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t row = (int32_t)(e / c4);
-    const int32_t c = (int32_t)(e - (int64_t)row * c4);
+    const int32_t row = (int32_t)(e / cpad);
+    const int32_t c = (int32_t)(e - (int64_t)row * cpad);
     int r = 0;
     while (r + 1 < nranges && row >= c_ranges[r + 1].row0) ++r;
     const ShiftRange R = c_ranges[r];
     int32_t s = 0;
-    if (c < nchans) {
+    {
+      // Padding channels (c >= nchans, all-zero data) repeat the last channel's delay, so they
+      // add no delay classes of their own to the last channel group.
+      const int32_t cc = c < nchans ? c : nchans - 1;
       // dm = start + i*step; a = 1/(f*f); b = 1/(fref*fref); tau = (k*dm)*(a-b);
       // x = tau/(tsamp*d) + 0.5; s = floor(x).  Explicit round-to-nearest intrinsics: no FMA.
       const double dm = __dadd_rn(R.dm_start, __dmul_rn((double)(row - R.row0), R.dm_step));
-      const double f = freqs[c];
+      const double f = freqs[cc];
       const double a = __ddiv_rn(1.0, __dmul_rn(f, f));
       const double b = __ddiv_rn(1.0, __dmul_rn(fref, fref));
       const double tau = __dmul_rn(__dmul_rn(kdm, dm), __dsub_rn(a, b));
@@ -52,18 +55,18 @@ __global__ void k_shift_table(const double* __restrict__ freqs, int32_t nchans, 
   }
 }
 
-cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t c4, double fref,
+cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t cpad, double fref,
                                double tsamp, const ShiftRange* ranges, int32_t nranges,
                                int32_t total_rows, int32_t* shifts, int32_t* err,
                                cudaStream_t st) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_ranges, ranges, sizeof(ShiftRange) * nranges, 0,
                                           cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
-  const int64_t total = (int64_t)total_rows * c4;
+  const int64_t total = (int64_t)total_rows * cpad;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  k_shift_table<<<(unsigned)blocks, 256, 0, st>>>(freqs, nchans, c4, fref, tsamp, nranges,
+  k_shift_table<<<(unsigned)blocks, 256, 0, st>>>(freqs, nchans, cpad, fref, tsamp, nranges,
                                                   total_rows, shifts, err);
   return cudaGetLastError();
 }
@@ -173,9 +176,9 @@ __global__ void k_decimate_u16(const uint16_t* __restrict__ in, int64_t in_strid
 }
 
 cudaError_t launch_decimate(const void* in, int in_is_u16, int64_t in_stride, uint16_t* out,
-                            int64_t out_stride, int32_t c4, int64_t n_out, cudaStream_t st) {
+                            int64_t out_stride, int32_t cpad, int64_t n_out, cudaStream_t st) {
   if (n_out <= 0) return cudaSuccess;
-  dim3 grid((unsigned)(((n_out + 3) / 4 + 255) / 256), (unsigned)c4);
+  dim3 grid((unsigned)(((n_out + 3) / 4 + 255) / 256), (unsigned)cpad);
   if (in_is_u16)
     k_decimate_u16<<<grid, 256, 0, st>>>(static_cast<const uint16_t*>(in), in_stride, out,
                                          out_stride, n_out);
@@ -188,27 +191,27 @@ cudaError_t launch_decimate(const void* in, int in_is_u16, int64_t in_stride, ui
 // ------------------------------------------------------------------ naive dedispersion
 
 template <typename T>
-__global__ void k_dedisp_naive(const T* __restrict__ xd, int64_t stride, int32_t c4, int64_t m0,
+__global__ void k_dedisp_naive(const T* __restrict__ xd, int64_t stride, int32_t cpad, int64_t m0,
                                int64_t nout, const int32_t* __restrict__ shifts,
                                int32_t* __restrict__ y, int64_t y_stride) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t i = blockIdx.y;
   if (j >= nout) return;
-  const int32_t* s = shifts + (int64_t)i * c4;
+  const int32_t* s = shifts + (int64_t)i * cpad;
   int32_t acc = 0;
-  for (int32_t c = 0; c < c4; ++c) acc += (int32_t)xd[(int64_t)c * stride + m0 + j + s[c]];
+  for (int32_t c = 0; c < cpad; ++c) acc += (int32_t)xd[(int64_t)c * stride + m0 + j + s[c]];
   y[(int64_t)i * y_stride + j] = acc;
 }
 
-cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t c4, cudaStream_t st) {
+cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t cpad, cudaStream_t st) {
   if (r.nout <= 0 || r.n_trials <= 0) return cudaSuccess;
   dim3 grid((unsigned)((r.nout + 255) / 256), (unsigned)r.n_trials);
   if (r.is_u16)
     k_dedisp_naive<uint16_t><<<grid, 256, 0, st>>>(static_cast<const uint16_t*>(r.xd), r.xd_stride,
-                                                   c4, r.m0, r.nout, r.shifts, r.y, r.y_stride);
+                                                   cpad, r.m0, r.nout, r.shifts, r.y, r.y_stride);
   else
     k_dedisp_naive<uint8_t><<<grid, 256, 0, st>>>(static_cast<const uint8_t*>(r.xd), r.xd_stride,
-                                                  c4, r.m0, r.nout, r.shifts, r.y, r.y_stride);
+                                                  cpad, r.m0, r.nout, r.shifts, r.y, r.y_stride);
   return cudaGetLastError();
 }
 

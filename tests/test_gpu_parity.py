@@ -145,6 +145,56 @@ def test_multirange_decimated_ragged_chunks():
     assert check(w, x[:sum(sizes)], sizes, 3) > 0
 
 
+def _tiled_regime(nchans=1001, nsamp=1 << 15):
+    """Channel width and DM steps in the regime of the 4096-channel workload (8-11 delay classes
+    per 8-channel group and 64-trial tile) at a size the oracle checks in full: 1001 channels
+    (neither a multiple of 8 nor of 16) from 1550 MHz down by 300/1024 MHz, 64 us, and eight
+    ranges x1..x128 whose trial counts leave ragged 64-trial tiles."""
+    ranges = (configs.DMRange(0.0, 0.0625, 150, 1), configs.DMRange(9.375, 0.125, 75, 2),
+              configs.DMRange(18.75, 0.15625, 130, 4), configs.DMRange(39.0625, 0.3125, 70, 8),
+              configs.DMRange(60.9375, 0.625, 40, 16), configs.DMRange(85.9375, 1.25, 30, 32),
+              configs.DMRange(123.4375, 2.5, 20, 64), configs.DMRange(173.4375, 5.0, 10, 128))
+    w = configs.mid(nsamp=nsamp, chunk_len=4096, n_streams=3, npulses=6, nchans=4096,
+                    ranges=ranges, index=9)
+    w.nchans = nchans
+    w.foff = -300.0 / 1024
+    w.pulses = tuple(configs.PulseSpec(p.dm * 0.2, min(p.t_ref, nsamp - 6000), p.width,
+                                       p.amp * 2.0) for p in w.pulses)
+    return w
+
+
+def test_kernel_choice():
+    """Ranges whose delay classes fit the tiled kernel's tables run on it (uint8 data in
+    512-sample tiles, decimated data in 256); x128 decimation (four channels of 255 x 128 do not
+    fit a 16-bit lane) and the tiny workload's 64 coarse channels (up to 63 classes per group)
+    run on the per-output kernel."""
+    w = _tiled_regime()
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1)
+    try:
+        got = [plan.kernel(r) for r in range(len(w.ranges))]
+    finally:
+        plan.close()
+    assert got == [(1, 512)] + [(1, 256)] * 6 + [(0, 0)]
+    t = configs.tiny()
+    plan = dd.Plan(t.freqs(), t.tsamp, t.ranges_array(), 4096, n_streams=1)
+    try:
+        assert plan.kernel(0) == (0, 0)
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("sizes,n_streams", [
+    ([1 << 15], 1),                            # one chunk: the whole input
+    ([4096] * 7 + [2048, 1920], 3),            # ragged chunks (multiples of d_max = 128)
+])
+def test_tiled_kernel_full_parity(sizes, n_streams):
+    """Every series of every trial of every range bit-exact against the oracle, and every
+    candidate, through the tiled kernel at the workload's channel width."""
+    w = _tiled_regime()
+    x = w.generate(_arrivals(w))
+    assert check(w, x[:sum(sizes)], sizes, n_streams) > 0
+
+
 def test_one_thread_per_output_kernel_matches():
     """The testing-aid kernel (DD_FLAG_NAIVE) obeys the same contract as the tiled one."""
     w = _small_multirange(nsamp=1 << 14)
