@@ -161,6 +161,7 @@ struct Slot {
 struct RangeKernel {
   bool tiled = false;
   int tt = 0;
+  int nseg = 0;
   int row_slot = 0;
   int zcap = 0;
   size_t smem = 0;
@@ -417,6 +418,7 @@ int plan_autotune(dd_plan_s* p) {
           break;
         }
         k.tt = tt;
+        k.nseg = tp.nseg;
         k.row_slot = tp.row_slot;
         k.zcap = tp.zcap;
         k.smem = tp.smem;
@@ -424,6 +426,11 @@ int plan_autotune(dd_plan_s* p) {
       ddk::TiledArgs A;
       A.xd = (l == 0) ? (const void*)s.ring1 : (const void*)s.ringd[l];
       A.xd_stride = (l == 0) ? p->R1 : p->Rd[l];
+      if (ddk::make_ring_map(&A.rows, A.xd, u16, A.xd_stride, p->Cp, k.nseg) != cudaSuccess) {
+        if (k.d_tabs != cur.d_tabs) cudaFree(k.d_tabs);
+        rc = fail(DD_ERR_CUDA, "autotune: tensor map of the ring could not be made");
+        break;
+      }
       A.m0 = 0;
       A.nout = std::max<int64_t>(1, (p->L - p->O + p->H) / d);
       A.nout = std::min<int64_t>(A.nout, p->L / d);
@@ -649,6 +656,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
           }
           k.tiled = true;
           k.tt = tt;
+          k.nseg = tp.nseg;
           k.row_slot = tp.row_slot;
           k.zcap = tp.zcap;
           k.smem = tp.smem;
@@ -828,6 +836,8 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       ddk::TiledArgs A;
       A.xd = R.xd;
       A.xd_stride = R.xd_stride;
+      if (ddk::make_ring_map(&A.rows, A.xd, R.is_u16, A.xd_stride, p->Cp, K.nseg) != cudaSuccess)
+        return fail(DD_ERR_CUDA, "tensor map of the ring could not be made");
       A.m0 = R.m0;
       A.nout = R.nout;
       A.y = R.y;

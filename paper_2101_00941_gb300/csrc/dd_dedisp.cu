@@ -10,20 +10,28 @@
 //     -- two 16-bit lanes, each the exact sum of four channels (4 x 255 x d < 2^16 for d <= 64)
 //     -- that each of its trials reads at its own base offset. The classes depend on the delay
 //     table only, so the plan computes them once (tiled_plan, below) as one fixed-size table per
-//     (trial tile, stage); the kernel never searches for them.
-//   * TMA (cp.async.bulk) brings each stage's 16 channel rows and its class table into shared
-//     memory kNStage stages ahead; completion is tracked by mbarriers with bounded waits.
+//     (trial tile, stage), together with a balanced split of the stage's word building over the
+//     warps; the kernel never searches for them.
+//   * TMA brings each stage's 16 channel rows (one 3-D tensor copy: every row from the same
+//     128-byte segment on, so each lands contiguous) and its class table into shared memory
+//     kNStage stages ahead; completion is tracked by mbarriers with bounded waits.
 //   * The main loop adds one pattern word per (trial, sample) with one DP2A: one 32-bit
 //     shared-memory load per eight channel-adds, for uint8 and uint16 (decimated) data alike.
 //
 // Software pipeline, one __syncthreads per stage s:
 //     TMA for stage s+kNStage-1 | build the words of stage s+1 | accumulate stage s
-// Words are built from aligned 32-bit loads and funnel shifts; the four-channel sums are formed
-// in SWAR lanes (bytes split into 16-bit lanes for uint8 data). Exact moments (S1, 128-bit S2)
-// of every series are added in the epilogue with integer atomics, so the search needs no second
-// statistics pass.
+// Words are built from 32-bit loads and funnel shifts; the four-channel sums are formed in SWAR
+// lanes (bytes split into 16-bit lanes for uint8 data). Where each class's channel rows start in
+// a stage buffer (row word and funnel shift) depends on where the stage's copy starts, so the
+// CTA works it out once per stage, one (class, channel) per thread, two stages ahead. Exact
+// moments (S1, 128-bit S2) of every series are added in the epilogue with integer atomics, so
+// the search needs no second statistics pass.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <climits>
 #include <cstring>
+#include <mutex>
 
 #include "dd_internal.h"
 
@@ -40,7 +48,8 @@ constexpr int kNG = 2;                      // groups per stage
 constexpr int kRows = kG * kNG;             // channel rows per stage
 constexpr int kNStage = 4;                  // staging buffers (rows + class table)
 constexpr int kMaxCls = 16;                 // classes per group
-constexpr int kMaxItems = 64;               // build items (64 units of one class) per group
+constexpr int kMaxWork = 8;                 // build ranges per warp and stage
+constexpr int kSegBytes = 128;              // inner extent of a staged-row copy (tensor map)
 
 // One delay class: its channels' first staged sample relative to the tile's first trial
 // (rel), and its words in the stage's pattern-word region.
@@ -54,19 +63,35 @@ struct ClsEntry {
 struct GroupTab {
   int16_t zstart[kTileTrials];  // stage word offset of each trial's sequence (0 for no trial)
   ClsEntry cls[kMaxCls];
-  uint16_t item[kMaxItems];     // class << 8 | segment of 64 units
-  int32_t ncls, nitem, pad0, pad1;
+  int32_t ncls, pad0, pad1, pad2;
 };
 
+// The stage's pattern-word build, cut at plan time into blocks of 32 units (one per lane) and
+// dealt to the warps in near-equal contiguous shares. A share is a few ranges, each within one
+// class: group << 4 | class, first block << 8, blocks << 16.
 struct StageTab {
   GroupTab g[kNG];
+  uint32_t work[kWarps][kMaxWork];
+  uint8_t nwork[kWarps];
+  int32_t xmin;  // smallest delay of the stage's rows for the tile's first trial
+  int32_t pad[3];
 };
 static_assert(sizeof(StageTab) % 16 == 0, "class tables are copied in 16-byte units");
+
+// Row addressing of every class of one stage: for each of its eight channels, the byte offset
+// of the row word holding the class's first sample within the stage buffer (8 x uint16) and the
+// funnel shift in bits that brings that sample to bit 0 (8 x uint8).
+struct AddrTab {
+  uint4 addr[kNG][kMaxCls];
+  uint2 sh[kNG][kMaxCls];
+};
+constexpr int kAddrEntries = kNG * kMaxCls * kG;  // one per thread of the first half of the CTA
+static_assert(kAddrEntries <= kThreads, "one addressing entry per thread");
 
 __host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 struct SmemLayout {
-  size_t raw, z, tab, phase, mbar, total;
+  size_t raw, z, tab, addr, mbar, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot, int zcap) {
@@ -78,8 +103,8 @@ __host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot,
   off = align16(off + (size_t)2 * zcap * zes);
   L.tab = off;
   off = align16(off + sizeof(StageTab) * kNStage);
-  L.phase = off;
-  off = align16(off + sizeof(int32_t) * kNStage * kRows);
+  L.addr = off;
+  off = align16(off + sizeof(AddrTab) * 2);
   L.mbar = off;
   off = align16(off + sizeof(unsigned long long) * kNStage);
   L.total = off;
@@ -88,6 +113,13 @@ __host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot,
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+template <int OFF>  // 32-bit shared-memory load at a byte address + OFF
+__device__ __forceinline__ uint32_t lds(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+  return v;
 }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
@@ -138,142 +170,140 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Warp-cooperative issue of one stage (one warp): lane k < kRows copies channel row k --
-// whole 16-byte units covering [m0 + j0 + s_first, m0 + j0 + s_last + TT) -- and records the
-// sample's phase within the first unit; lane kRows copies the stage's class table. Lane 0 first
-// arms the stage's mbarrier with the total byte count.
-template <typename T, int TT>
-__device__ void issue_stage(const TiledArgs& a, int stage, int nstages, T* raw_buf,
-                            StageTab* tab_buf, int32_t* phase_buf, unsigned long long* bar,
-                            int trial0, int ntr, int64_t j0, int lane) {
-  constexpr int A = 16 / (int)sizeof(T);  // elements per 16 bytes
-  const int c = stage * kRows + lane;
-  const bool mine = lane < kRows && c < a.cpad;
-  int64_t a0 = 0;
-  uint32_t nb = 0;
-  if (mine) {
-    const int32_t smin = __ldg(a.shifts + (int64_t)trial0 * a.cpad + c);
-    const int32_t smax = __ldg(a.shifts + (int64_t)(trial0 + ntr - 1) * a.cpad + c);
-    const int64_t start = a.m0 + j0 + smin;
-    a0 = start & ~(int64_t)(A - 1);
-    const int64_t end = a.m0 + j0 + smax + TT;
-    nb = (uint32_t)(((end - a0) * (int64_t)sizeof(T) + 15) & ~int64_t(15));
-    phase_buf[lane] = (int32_t)(start - a0);
-  }
-  if (lane == kRows) nb = (uint32_t)sizeof(StageTab);
-  __syncwarp();  // the phases written above are released by lane 0's arrive below
-  uint32_t total = nb;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) total += __shfl_xor_sync(0xffffffffu, total, off);
-  if (lane == 0) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(bar, total);
-  }
-  __syncwarp();
-  if (mine)
-    bulk_g2s(raw_buf + (size_t)lane * a.row_slot,
-             static_cast<const T*>(a.xd) + (int64_t)c * a.xd_stride + a0, nb, bar);
-  if (lane == kRows)
-    bulk_g2s(tab_buf, a.tabs + ((size_t)blockIdx.x * nstages + stage) * sizeof(StageTab),
-             (uint32_t)sizeof(StageTab), bar);
+// First row segment of a stage's copy: every row is copied from the segment holding sample
+// m0 + j0 + xmin on, xmin being the smallest delay of the stage's rows.
+template <typename T>
+__device__ __forceinline__ int64_t first_seg(const TiledArgs& a, int64_t j0, int32_t xmin) {
+  constexpr int SEG = kSegBytes / (int)sizeof(T);  // elements per segment
+  return (a.m0 + j0 + xmin) / SEG;
 }
+
+__device__ __forceinline__ int32_t stage_xmin(const TiledArgs& a, int stage, int nstages) {
+  if (stage >= nstages) return 0;
+  return __ldg(&reinterpret_cast<const StageTab*>(a.tabs)[(size_t)blockIdx.x * nstages + stage]
+                    .xmin);
+}
+
+// Issue of one stage by one thread: one tensor copy of the stage's 16 rows (segments
+// [first_seg, first_seg + nseg) of each; rows past the padded channels read as zeros) and one
+// bulk copy of its class table, after arming the stage's mbarrier with their bytes.
+template <typename T>
+__device__ __forceinline__ void issue_stage(const TiledArgs& a, int stage, int nstages,
+                                            T* raw_buf, StageTab* tab_buf,
+                                            unsigned long long* bar, int32_t xmin, int64_t j0) {
+  const uint32_t row_bytes = (uint32_t)a.row_slot * (uint32_t)sizeof(T);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect_tx(bar, kRows * row_bytes + (uint32_t)sizeof(StageTab));
+  const int32_t seg = (int32_t)first_seg<T>(a, j0, xmin);
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(raw_buf)),
+      "l"(reinterpret_cast<uint64_t>(&a.rows)), "r"(0), "r"(seg), "r"(stage * kRows),
+      "r"(smem_addr(bar))
+      : "memory");
+  bulk_g2s(tab_buf, a.tabs + ((size_t)blockIdx.x * nstages + stage) * sizeof(StageTab),
+           (uint32_t)sizeof(StageTab), bar);
+}
+
+// One addressing entry of a stage: entry e = (group, class, channel). The row's copy starts at
+// segment first_seg (issue_stage), so the class's first sample sits
+// m0 + j0 + s_first - first_seg * (segment elements) + rel elements into the row. Its inputs come
+// from the class table and the delay table in global memory (the staged copy of the table may
+// still be in flight), loaded one iteration before the entry is formed.
+struct AddrInputs {
+  int32_t ncls;  // classes of the entry's group (0: no such group)
+  int32_t rel;
+  int32_t smin;
+  int32_t xmin;
+};
+
+__device__ __forceinline__ AddrInputs addr_inputs(const TiledArgs& a, int stage, int nstages,
+                                                  int ngroups, int trial0, int e) {
+  AddrInputs in{0, 0, 0, 0};
+  const int gl = e / (kMaxCls * kG), p = (e / kG) % kMaxCls, k = e % kG;
+  if (stage < nstages && stage * kNG + gl < ngroups) {
+    const StageTab* st =
+        &reinterpret_cast<const StageTab*>(a.tabs)[(size_t)blockIdx.x * nstages + stage];
+    const GroupTab* gt = &st->g[gl];
+    in.xmin = __ldg(&st->xmin);
+    in.ncls = __ldg(&gt->ncls);
+    in.rel = __ldg(&gt->cls[p].rel[k]);  // the table is zero past the group's classes
+    in.smin = __ldg(a.shifts + (int64_t)trial0 * a.cpad + stage * kRows + gl * kG + k);
+  }
+  return in;
+}
+
+template <typename T>
+__device__ __forceinline__ void addr_entry(const TiledArgs& a, const AddrInputs& in, int64_t j0,
+                                           int e, AddrTab* at) {
+  constexpr int SEG = kSegBytes / (int)sizeof(T);
+  const int gl = e / (kMaxCls * kG), p = (e / kG) % kMaxCls, k = e % kG;
+  if (p >= in.ncls) return;
+  const int row = gl * kG + k;
+  const int ph = (int)(a.m0 + j0 + in.smin - first_seg<T>(a, j0, in.xmin) * SEG);
+  const uint32_t byte = (uint32_t)(row * a.row_slot + in.rel + ph) * (uint32_t)sizeof(T);
+  reinterpret_cast<uint16_t*>(&at->addr[gl][p])[k] = (uint16_t)(byte & ~3u);
+  reinterpret_cast<uint8_t*>(&at->sh[gl][p])[k] = (uint8_t)((byte & 3u) * 8u);
+}
+
+// The eight channel rows of one class, as one lane reads them: shared-memory byte address of
+// the row word holding its first unit, and the funnel shift of each channel.
+struct RowItem {
+  uint32_t addr[kG];
+  uint32_t sh[kG];
+};
 
 template <typename T>
 struct Word;
 
-// Row access shared by both data types: for each of the group's eight channels, the row word
-// holding the class's sample 0 and the bit phase of that sample in it. A build unit starts on a
-// multiple of the samples per row word, so the phase is fixed per class: set once per item.
-struct RowItem {
-  const uint32_t* rp[kG];
-  uint32_t sh[kG];
-};
-
-template <int EPW>  // elements per 32-bit row word
-__device__ __forceinline__ RowItem row_item(const uint32_t* rows, int row_words, int g,
-                                            const int (&col)[kG]) {
-  RowItem it;
-#pragma unroll
-  for (int k = 0; k < kG; ++k) {
-    it.rp[k] = rows + (size_t)(kG * g + k) * row_words + col[k] / EPW;
-    it.sh[k] = (uint32_t)(col[k] % EPW) * (32u / EPW);
-  }
-  return it;
-}
-
-// uint8 data: a lane builds 8 consecutive pattern words (two units of 4) from three row words
-// per channel; bytes are split into even/odd 16-bit lanes so that four channels add without
-// carries, then the two four-channel sums of each sample are paired into its word.
+// uint8 data: pattern word = (sum of channels 0-3) | (sum of channels 4-7) << 16 of one sample.
+// A lane builds units u and u + 32 (pattern words 4u .. 4u + 3 and 4u + 128 .. 4u + 131), each
+// from two row words per channel; lanes take consecutive units, so every load and store is
+// free of bank conflicts. Bytes are split into even/odd 16-bit lanes so that four channels add
+// without carries, then the two four-channel sums of each sample are paired into its word.
 template <>
 struct Word<uint8_t> {
   static constexpr int kUnit = 4;  // pattern words per unit
-  static constexpr int kEPW = 4;
-  static __device__ __forceinline__ void sums(const uint32_t (&v)[kG], uint4& out) {
+  template <int OFF>
+  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* dst) {
     uint32_t elo = 0, olo = 0, ehi = 0, ohi = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      elo += v[k] & 0x00FF00FFu;             // samples 0, 2
-      olo += __byte_perm(v[k], 0, 0x4341);   // samples 1, 3
-      ehi += v[k + 4] & 0x00FF00FFu;
-      ohi += __byte_perm(v[k + 4], 0, 0x4341);
-    }
-    out.x = __byte_perm(elo, ehi, 0x5410);  // sample 0: (ch0-3 sum) | (ch4-7 sum) << 16
-    out.y = __byte_perm(olo, ohi, 0x5410);  // sample 1
-    out.z = __byte_perm(elo, ehi, 0x7632);  // sample 2
-    out.w = __byte_perm(olo, ohi, 0x7632);  // sample 3
-  }
-  // units 2p and 2p + 1 = pattern words 8p .. 8p + 7
-  static __device__ __forceinline__ void build2(const RowItem& it, int p, bool second,
-                                                uint32_t* dst) {
-    uint32_t a[kG], b[kG];
-#pragma unroll
-    for (int k = 0; k < kG; ++k) {
-      const uint32_t w0 = it.rp[k][2 * p], w1 = it.rp[k][2 * p + 1], w2 = it.rp[k][2 * p + 2];
-      a[k] = __funnelshift_r(w0, w1, it.sh[k]);
-      b[k] = __funnelshift_r(w1, w2, it.sh[k]);
+      const uint32_t a = __funnelshift_r(lds<OFF>(it.addr[k]), lds<OFF + 4>(it.addr[k]), it.sh[k]);
+      const uint32_t b =
+          __funnelshift_r(lds<OFF>(it.addr[k + 4]), lds<OFF + 4>(it.addr[k + 4]), it.sh[k + 4]);
+      elo += a & 0x00FF00FFu;            // samples 0, 2
+      olo += __byte_perm(a, 0, 0x4341);  // samples 1, 3
+      ehi += b & 0x00FF00FFu;
+      ohi += __byte_perm(b, 0, 0x4341);
     }
     uint4 o;
-    sums(a, o);
-    reinterpret_cast<uint4*>(dst)[2 * p] = o;
-    if (second) {
-      sums(b, o);
-      reinterpret_cast<uint4*>(dst)[2 * p + 1] = o;
-    }
+    o.x = __byte_perm(elo, ehi, 0x5410);  // sample 0: (ch0-3 sum) | (ch4-7 sum) << 16
+    o.y = __byte_perm(olo, ohi, 0x5410);  // sample 1
+    o.z = __byte_perm(elo, ehi, 0x7632);  // sample 2
+    o.w = __byte_perm(olo, ohi, 0x7632);  // sample 3
+    *reinterpret_cast<uint4*>(dst) = o;
   }
 };
 
-// uint16 data: a lane builds 4 consecutive pattern words (two units of 2): 16-bit lanes add
-// four channels without carries (4 x 255 x d < 2^16).
+// uint16 data: a lane builds units u and u + 32 (pattern words 2u, 2u + 1 and 2u + 64, 2u + 65)
+// from two row words per channel; 16-bit lanes add four channels without carries
+// (4 x 255 x d < 2^16).
 template <>
 struct Word<uint16_t> {
   static constexpr int kUnit = 2;
-  static constexpr int kEPW = 2;
-  // units 2p and 2p + 1 = pattern words 4p .. 4p + 3
-  static __device__ __forceinline__ void build2(const RowItem& it, int p, bool second,
-                                                uint32_t* dst) {
-    uint32_t alo = 0, ahi = 0, blo = 0, bhi = 0;
+  template <int OFF>
+  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* dst) {
+    uint32_t lo = 0, hi = 0;
 #pragma unroll
-    for (int k = 0; k < kG; ++k) {
-      const uint32_t w0 = it.rp[k][2 * p], w1 = it.rp[k][2 * p + 1], w2 = it.rp[k][2 * p + 2];
-      const uint32_t a = __funnelshift_r(w0, w1, it.sh[k]);  // samples 0, 1
-      const uint32_t b = __funnelshift_r(w1, w2, it.sh[k]);  // samples 2, 3
-      if (k < 4) {
-        alo += a;
-        blo += b;
-      } else {
-        ahi += a;
-        bhi += b;
-      }
+    for (int k = 0; k < 4; ++k) {
+      lo += __funnelshift_r(lds<OFF>(it.addr[k]), lds<OFF + 4>(it.addr[k]), it.sh[k]);
+      hi += __funnelshift_r(lds<OFF>(it.addr[k + 4]), lds<OFF + 4>(it.addr[k + 4]), it.sh[k + 4]);
     }
     uint2 o;
-    o.x = __byte_perm(alo, ahi, 0x5410);  // sample 0
-    o.y = __byte_perm(alo, ahi, 0x7632);  // sample 1
-    reinterpret_cast<uint2*>(dst)[2 * p] = o;
-    if (second) {
-      o.x = __byte_perm(blo, bhi, 0x5410);  // sample 2
-      o.y = __byte_perm(blo, bhi, 0x7632);  // sample 3
-      reinterpret_cast<uint2*>(dst)[2 * p + 1] = o;
-    }
+    o.x = __byte_perm(lo, hi, 0x5410);  // sample 0
+    o.y = __byte_perm(lo, hi, 0x7632);  // sample 1
+    *reinterpret_cast<uint2*>(dst) = o;
   }
 };
 
@@ -281,40 +311,62 @@ __device__ __forceinline__ uint32_t dot(uint32_t z, uint32_t acc) {
   return __dp2a_lo(z, 0x0101u, acc);  // acc + (ch0-3 sum) + (ch4-7 sum)
 }
 
-// Build every pattern word of one stage. The plan cut the work into items of 64 units of one
-// class; warp w takes items w, w + kWarps, ... and each lane builds two adjacent units.
+// Build every pattern word of one stage: warp w walks its ranges of the plan's work list; lane
+// l builds unit 32 * b + l of every block b of a range, two blocks per pass.
 template <typename T>
-__device__ __forceinline__ void build_stage(const StageTab& tb, int ng, const T* rawb,
-                                            const int32_t* phase, int row_slot, uint32_t* Zs,
-                                            int warp, int lane) {
+__device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& at, uint32_t rawb,
+                                            uint32_t* Zs, int warp, int lane) {
   constexpr int U = Word<T>::kUnit;
-  const int n0 = tb.g[0].nitem;
-  const int n1 = n0 + (ng > 1 ? tb.g[1].nitem : 0);
-  const uint32_t* rows = reinterpret_cast<const uint32_t*>(rawb);
-  const int row_words = row_slot * (int)sizeof(T) / 4;
-  for (int k = warp; k < n1; k += kWarps) {
-    const int gi = k >= n0 ? 1 : 0;
-    const GroupTab& gt = tb.g[gi];
-    const uint32_t itw = gt.item[k - (gi ? n0 : 0)];
-    const ClsEntry& e = gt.cls[itw >> 8];
-    int col[kG];
+  const int nw = tb.nwork[warp];
+  for (int w = 0; w < nw; ++w) {
+    const uint32_t wk = tb.work[warp][w];
+    const int gi = (int)((wk >> 4) & 1), p = (int)(wk & 15);
+    const int b0 = (int)((wk >> 8) & 255), nb = (int)(wk >> 16);
+    const int zlen = tb.g[gi].cls[p].zlen;
+    int u = 32 * b0 + lane;
+    const uint4 ad = at.addr[gi][p];
+    const uint2 sv = at.sh[gi][p];
+    const uint32_t base = rawb + 4u * (uint32_t)u;  // one row word per unit
+    RowItem it;
+    it.addr[0] = base + (ad.x & 0xFFFFu);
+    it.addr[1] = base + (ad.x >> 16);
+    it.addr[2] = base + (ad.y & 0xFFFFu);
+    it.addr[3] = base + (ad.y >> 16);
+    it.addr[4] = base + (ad.z & 0xFFFFu);
+    it.addr[5] = base + (ad.z >> 16);
+    it.addr[6] = base + (ad.w & 0xFFFFu);
+    it.addr[7] = base + (ad.w >> 16);
+    // the funnel shift uses the low 5 bits of its amount
+    it.sh[0] = sv.x;
+    it.sh[1] = sv.x >> 8;
+    it.sh[2] = sv.x >> 16;
+    it.sh[3] = sv.x >> 24;
+    it.sh[4] = sv.y;
+    it.sh[5] = sv.y >> 8;
+    it.sh[6] = sv.y >> 16;
+    it.sh[7] = sv.y >> 24;
+    uint32_t* dst = Zs + tb.g[gi].cls[p].zoff + U * u;
+    for (int b = 0; b < nb; b += 2) {
+      if (u * U < zlen) Word<T>::template unit<0>(it, dst);
+      if (b + 1 < nb && (u + 32) * U < zlen) Word<T>::template unit<128>(it, dst + 32 * U);
 #pragma unroll
-    for (int q = 0; q < kG; ++q) col[q] = e.rel[q] + phase[kG * gi + q];
-    const RowItem it = row_item<Word<T>::kEPW>(rows, row_words, gi, col);
-    const int pu = (int)(itw & 255) * 32 + lane;  // unit pair: units 2pu, 2pu + 1
-    if (2 * pu * U < e.zlen) Word<T>::build2(it, pu, (2 * pu + 1) * U < e.zlen, Zs + e.zoff);
+      for (int k = 0; k < kG; ++k) it.addr[k] += 256u;  // 64 units further
+      u += 64;
+      dst += 64 * U;
+    }
   }
 }
 
 template <typename T, int TT>
-__global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a) {
+__global__ void __launch_bounds__(kThreads, 1)
+    k_dedisp_tiled(const __grid_constant__ TiledArgs a) {
   constexpr int KT = TT / 32;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];  // tensor copies land 128-aligned
   const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap);
   T* raw = reinterpret_cast<T*>(smem + SL.raw);
   uint32_t* Zbuf = reinterpret_cast<uint32_t*>(smem + SL.z);
   StageTab* tab = reinterpret_cast<StageTab*>(smem + SL.tab);
-  int32_t* phase = reinterpret_cast<int32_t*>(smem + SL.phase);
+  AddrTab* atab = reinterpret_cast<AddrTab*>(smem + SL.addr);
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + SL.mbar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -330,17 +382,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  // row addressing of stages 0 and 1; stage s + 2 is formed during iteration s from inputs
+  // loaded during iteration s - 1 (the prologue for s = 0)
+  AddrInputs ain{0, 0, 0, 0};
+  {
+    const int s0 = tid / kAddrEntries;
+    if (s0 < 2) {
+      const AddrInputs in0 = addr_inputs(a, s0, nstages, ngroups, trial0, tid % kAddrEntries);
+      addr_entry<T>(a, in0, j0, tid % kAddrEntries, &atab[s0]);
+    }
+    if (tid < kAddrEntries) ain = addr_inputs(a, 2, nstages, ngroups, trial0, tid);
+  }
   __syncthreads();
   // stages whose copies have been issued: kNStage in the prologue, then one per iteration s >= 1
   // (the same count in every thread)
   int issued = min(kNStage, nstages);
-  if (warp == kWarps - 1) {
+  int32_t xmin_next = 0;  // first delay of the next stage to issue (issuing thread)
+  if (tid == kThreads - 32) {
     for (int s = 0; s < kNStage && s < nstages; ++s)
-      issue_stage<T, TT>(a, s, nstages, raw + (size_t)s * stage_elems, &tab[s],
-                         phase + s * kRows, &mbar[s], trial0, ntr, j0, lane);
+      issue_stage<T>(a, s, nstages, raw + (size_t)s * stage_elems, &tab[s], &mbar[s],
+                     stage_xmin(a, s, nstages), j0);
+    xmin_next = stage_xmin(a, kNStage, nstages);
   }
   bool ok0 = mbar_wait_bounded(&mbar[0], 0);
-  if (ok0) build_stage<T>(tab[0], min(kNG, ngroups), raw, phase, a.row_slot, Zbuf, warp, lane);
+  if (ok0) build_stage<T>(tab[0], atab[0], smem_addr(raw), Zbuf, warp, lane);
   bool aborted = __syncthreads_or(!ok0);
   int s_abort = 0;  // first stage whose copies may still be in flight
 
@@ -357,10 +422,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
     if (s >= 1 && s + kNStage - 1 < nstages) {
       const int s2 = s + kNStage - 1;
       const int b2 = s2 % kNStage;
-      if (warp == kWarps - 1)
-        issue_stage<T, TT>(a, s2, nstages, raw + (size_t)b2 * stage_elems, &tab[b2],
-                           phase + b2 * kRows, &mbar[b2], trial0, ntr, j0, lane);
+      if (tid == kThreads - 32) {
+        issue_stage<T>(a, s2, nstages, raw + (size_t)b2 * stage_elems, &tab[b2], &mbar[b2],
+                       xmin_next, j0);
+        xmin_next = stage_xmin(a, s2 + 1, nstages);
+      }
       issued = s2 + 1;
+    }
+    // row addressing of stage s + 2, into the buffer stage s used (read during iteration s - 1)
+    if (tid < kAddrEntries) {
+      if (s + 2 < nstages) addr_entry<T>(a, ain, j0, tid, &atab[s & 1]);
+      ain = addr_inputs(a, s + 3, nstages, ngroups, trial0, tid);
     }
     // (2) pattern words of stage s + 1
     bool ok = true;
@@ -368,9 +440,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dedisp_tiled(const TiledArgs a)
       const int b1 = (s + 1) % kNStage;
       ok = mbar_wait_bounded(&mbar[b1], (uint32_t)(((s + 1) / kNStage) & 1));
       if (ok)
-        build_stage<T>(tab[b1], min(kNG, ngroups - (s + 1) * kNG), raw + (size_t)b1 * stage_elems,
-                       phase + b1 * kRows, a.row_slot, Zbuf + (size_t)((s + 1) & 1) * a.zcap,
-                       warp, lane);
+        build_stage<T>(tab[b1], atab[(s + 1) & 1], smem_addr(raw + (size_t)b1 * stage_elems),
+                       Zbuf + (size_t)((s + 1) & 1) * a.zcap, warp, lane);
     }
     // (3) accumulate stage s
     {
@@ -468,6 +539,40 @@ cudaError_t prepare_t(size_t smem) {
 
 }  // namespace
 
+namespace {
+
+// Cut a stage's classes into blocks of 32 units (U pattern words each) and deal them to the
+// warps in contiguous shares of ceil(blocks / warps); false if a share needs more ranges than
+// a warp's list holds or a class more blocks than a range can name.
+bool deal_work(StageTab& st, int U) {
+  int total = 0;
+  for (int gl = 0; gl < kNG; ++gl)
+    for (int p = 0; p < st.g[gl].ncls; ++p) total += (st.g[gl].cls[p].zlen / U + 31) / 32;
+  const int share = (total + kWarps - 1) / kWarps;
+  int w = 0, used = 0;
+  for (int gl = 0; gl < kNG; ++gl)
+    for (int p = 0; p < st.g[gl].ncls; ++p) {
+      const int nb = (st.g[gl].cls[p].zlen / U + 31) / 32;
+      if (nb > 255) return false;
+      int b = 0;
+      while (b < nb) {
+        const int take = std::min(nb - b, share - used);
+        if (w >= kWarps || st.nwork[w] >= kMaxWork) return false;
+        st.work[w][st.nwork[w]++] =
+            (uint32_t)(gl << 4 | p) | (uint32_t)b << 8 | (uint32_t)take << 16;
+        b += take;
+        used += take;
+        if (used == share) {
+          ++w;
+          used = 0;
+        }
+      }
+    }
+  return true;
+}
+
+}  // namespace
+
 int tiled_tile_samples(int is_u16, int choice) {
   // preferred time tile first, a smaller one when the first does not fit shared memory
   if (!is_u16) return choice == 0 ? 512 : 256;
@@ -488,7 +593,7 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
   const int D = kTileTrials, NG = kNG, U = u16 ? 2 : 4;
   const int ngroups = cpad / kG, nstages = (ngroups + NG - 1) / NG;
   const int ntiles = (ntr + D - 1) / D;
-  int64_t spread = 0, zcap = 0;
+  int64_t spread = 0, zcap = 0, span = 0;
   std::vector<StageTab> out((size_t)ntiles * nstages);
   for (int ti = 0; ti < ntiles; ++ti) {
     const int t0 = ti * D, n = std::min(D, ntr - t0);
@@ -501,6 +606,15 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
     for (int s = 0; s < nstages; ++s) {
       StageTab& st = out[(size_t)ti * nstages + s];
       std::memset(&st, 0, sizeof st);
+      // the rows' common copy window: from the smallest first-trial delay to the largest
+      // last-trial delay of the stage's channels
+      int32_t xmin = INT32_MAX, xmax = 0;
+      for (int c = s * kRows; c < std::min(cpad, (s + 1) * kRows); ++c) {
+        xmin = std::min(xmin, tab[(int64_t)t0 * cpad + c]);
+        xmax = std::max(xmax, tab[(int64_t)(t0 + n - 1) * cpad + c]);
+      }
+      st.xmin = xmin;
+      span = std::max<int64_t>(span, (int64_t)xmax - xmin);
       int words = 0;
       for (int gl = 0; gl < NG && s * NG + gl < ngroups; ++gl) {
         const int g = s * NG + gl;
@@ -532,7 +646,6 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
           }
           cls_of[i] = p;
         }
-        int nitem = 0;
         int zoff[kMaxCls];
         for (int p = 0; p < ncls; ++p) {
           const int zlen = (tt + cmax[p] - cmin[p] + 3) & ~3;
@@ -545,35 +658,32 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
           }
           e.zoff = (int16_t)words;
           e.zlen = (int16_t)zlen;
-          // one item = 32 lanes x 2 units
-          const int nseg = (zlen / U + 63) / 64;
-          for (int q = 0; q < nseg; ++q) {
-            if (nitem >= kMaxItems) return P;
-            gt.item[nitem++] = (uint16_t)((p << 8) | q);
-          }
           words += zlen;
           if (words > 32767) return P;
         }
         for (int i = 0; i < n; ++i)
           gt.zstart[i] = (int16_t)(zoff[cls_of[i]] + b[i] - cmin[cls_of[i]]);
         gt.ncls = ncls;
-        gt.nitem = nitem;
       }
+      if (!deal_work(st, U)) return P;
       zcap = std::max<int64_t>(zcap, words);
     }
   }
   if (spread > 65536) return P;
-  const int A = u16 ? 8 : 16;
+  const int SEG = kSegBytes / (u16 ? 2 : 1);
   P.tt = tt;
-  // staged row: up to A-1 elements of alignment in front, 16-byte rounding behind, and 16
-  // elements the word-wise build may read past the last word it uses
-  P.row_slot = (int)(((tt + spread + 2 * A + 16) + A - 1) / A * A);
+  // staged row: the stage's window (span + tt samples) from up to SEG - 1 samples into its
+  // first segment, and 32 samples the word-wise build may read past the last word it uses
+  P.nseg = (int)((span + tt + 32 + 2 * SEG - 2) / SEG);
+  if (P.nseg > 255) return P;
+  P.row_slot = P.nseg * SEG;
   P.zcap = (int)((std::max<int64_t>(zcap, 4) + 3) / 4 * 4);
   P.smem = smem_layout(u16 ? 2 : 1, 4, P.row_slot, P.zcap).total;
   P.tab_bytes = out.size() * sizeof(StageTab);
   P.tabs.resize(P.tab_bytes);
   std::memcpy(P.tabs.data(), out.data(), P.tab_bytes);
-  P.ok = P.smem <= 200 * 1024;
+  // addressing entries hold byte offsets within a stage buffer as uint16
+  P.ok = P.smem <= 200 * 1024 && (size_t)kRows * P.row_slot * (u16 ? 2 : 1) <= 65535;
   return P;
 }
 
@@ -583,6 +693,45 @@ cudaError_t prepare_tiled(int is_u16, int tt, size_t smem) {
   if (is_u16 && tt == 256) return prepare_t<uint16_t, 256>(smem);
   if (is_u16 && tt == 128) return prepare_t<uint16_t, 128>(smem);
   return cudaErrorInvalidValue;
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+cudaError_t make_ring_map(CUtensorMap* map, const void* ring, int is_u16, int64_t stride,
+                          int32_t cpad, int nseg) {
+  const int es = is_u16 ? 2 : 1;
+  const int64_t seg = kSegBytes / es;
+  if ((stride * es) % kSegBytes || nseg < 1 || nseg > 255 || cpad < 1 ||
+      (reinterpret_cast<uintptr_t>(ring) & 15))
+    return cudaErrorInvalidValue;
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)seg, (cuuint64_t)(stride / seg), (cuuint64_t)cpad};
+  const cuuint64_t strides[2] = {(cuuint64_t)kSegBytes, (cuuint64_t)(stride * es)};
+  const cuuint32_t box[3] = {(cuuint32_t)seg, (cuuint32_t)nseg, (cuuint32_t)kRows};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r =
+      fn(map, is_u16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
+         const_cast<void*>(ring), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st) {

@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units (not part of the C ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,6 +84,7 @@ struct TiledArgs {
   int32_t zcap;            // pattern words per stage
   const uint8_t* tabs;     // delay-class tables of the range, one per (trial tile, stage)
   int32_t* err;            // bit 0: a bounded wait ran out
+  CUtensorMap rows;        // the ring as [Cp][xd_stride / seg][seg] (make_ring_map)
 };
 
 // Plan of the tiled kernel for one range (host): tile shape, shared-memory sizes and the
@@ -90,6 +92,7 @@ struct TiledArgs {
 struct TiledPlan {
   bool ok = false;
   int tt = 0;
+  int nseg = 0;            // 128-byte segments per staged channel row
   int row_slot = 0;
   int zcap = 0;
   size_t smem = 0;
@@ -101,6 +104,12 @@ int tiled_tile_samples(int is_u16, int choice);
 TiledPlan tiled_plan(const int32_t* shifts, int ntr, int cpad, int decimation, int tt);
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st);
+
+// Tensor map of a channel-major ring (uint8, or uint16 when is_u16) for the tiled kernel's
+// stage copies: dims {128-byte segment, segments per row, cpad rows}, box {segment, nseg, 16}.
+// The row stride must be a multiple of 128 bytes. Host only; no device work.
+cudaError_t make_ring_map(CUtensorMap* map, const void* ring, int is_u16, int64_t stride,
+                          int32_t cpad, int nseg);
 
 // Record `msg` as the calling thread's last error (dd_last_error) and return `code`.
 int report_error(int code, const char* msg);
