@@ -253,6 +253,13 @@ struct RowItem {
   uint32_t sh[kG];
 };
 
+// Row word of channel k at byte offset OFF, shifted to the class's first sample (the funnel
+// shift uses the low 5 bits of its amount).
+template <int OFF>
+__device__ __forceinline__ uint32_t row_word(const RowItem& it, int k) {
+  return __funnelshift_r(lds<OFF>(it.addr[k]), lds<OFF + 4>(it.addr[k]), it.sh[k]);
+}
+
 template <typename T>
 struct Word;
 
@@ -269,9 +276,7 @@ struct Word<uint8_t> {
     uint32_t elo = 0, olo = 0, ehi = 0, ohi = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t a = __funnelshift_r(lds<OFF>(it.addr[k]), lds<OFF + 4>(it.addr[k]), it.sh[k]);
-      const uint32_t b =
-          __funnelshift_r(lds<OFF>(it.addr[k + 4]), lds<OFF + 4>(it.addr[k + 4]), it.sh[k + 4]);
+      const uint32_t a = row_word<OFF>(it, k), b = row_word<OFF>(it, k + 4);
       elo += a & 0x00FF00FFu;            // samples 0, 2
       olo += __byte_perm(a, 0, 0x4341);  // samples 1, 3
       ehi += b & 0x00FF00FFu;
@@ -297,8 +302,8 @@ struct Word<uint16_t> {
     uint32_t lo = 0, hi = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      lo += __funnelshift_r(lds<OFF>(it.addr[k]), lds<OFF + 4>(it.addr[k]), it.sh[k]);
-      hi += __funnelshift_r(lds<OFF>(it.addr[k + 4]), lds<OFF + 4>(it.addr[k + 4]), it.sh[k + 4]);
+      lo += row_word<OFF>(it, k);      // samples 0, 1 of channels 0-3
+      hi += row_word<OFF>(it, k + 4);  // of channels 4-7
     }
     uint2 o;
     o.x = __byte_perm(lo, hi, 0x5410);  // sample 0
@@ -336,15 +341,11 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
     it.addr[5] = base + (ad.z >> 16);
     it.addr[6] = base + (ad.w & 0xFFFFu);
     it.addr[7] = base + (ad.w >> 16);
-    // the funnel shift uses the low 5 bits of its amount
-    it.sh[0] = sv.x;
-    it.sh[1] = sv.x >> 8;
-    it.sh[2] = sv.x >> 16;
-    it.sh[3] = sv.x >> 24;
-    it.sh[4] = sv.y;
-    it.sh[5] = sv.y >> 8;
-    it.sh[6] = sv.y >> 16;
-    it.sh[7] = sv.y >> 24;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      it.sh[k] = sv.x >> (8 * k);
+      it.sh[k + 4] = sv.y >> (8 * k);
+    }
     uint32_t* dst = Zs + tb.g[gi].cls[p].zoff + U * u;
     for (int b = 0; b < nb; b += 2) {
       if (u * U < zlen) Word<T>::template unit<0>(it, dst);
@@ -575,8 +576,8 @@ bool deal_work(StageTab& st, int U) {
 
 int tiled_tile_samples(int is_u16, int choice) {
   // preferred time tile first, a smaller one when the first does not fit shared memory
-  if (!is_u16) return choice == 0 ? 512 : 256;
-  return choice == 0 ? 256 : 128;
+  (void)is_u16;
+  return choice == 0 ? 512 : 256;
 }
 
 // Host: delay classes of every (trial tile, stage) of one range, as the kernel reads them.
@@ -690,8 +691,8 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem) {
   if (!is_u16 && tt == 512) return prepare_t<uint8_t, 512>(smem);
   if (!is_u16 && tt == 256) return prepare_t<uint8_t, 256>(smem);
+  if (is_u16 && tt == 512) return prepare_t<uint16_t, 512>(smem);
   if (is_u16 && tt == 256) return prepare_t<uint16_t, 256>(smem);
-  if (is_u16 && tt == 128) return prepare_t<uint16_t, 128>(smem);
   return cudaErrorInvalidValue;
 }
 
@@ -738,8 +739,8 @@ cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st
   if (a.nout <= 0 || a.n_trials <= 0) return cudaSuccess;
   if (!is_u16 && tt == 512) return launch_tiled_t<uint8_t, 512>(a, st);
   if (!is_u16 && tt == 256) return launch_tiled_t<uint8_t, 256>(a, st);
+  if (is_u16 && tt == 512) return launch_tiled_t<uint16_t, 512>(a, st);
   if (is_u16 && tt == 256) return launch_tiled_t<uint16_t, 256>(a, st);
-  if (is_u16 && tt == 128) return launch_tiled_t<uint16_t, 128>(a, st);
   return cudaErrorInvalidValue;
 }
 
