@@ -38,6 +38,10 @@ METRIC = "DM-trial·samples/s dedispersed"
 UNIT = "DM-trial·samples/s"
 # Integer ALU roofline: 152 SMs x 128 int32 lanes per clock (ALU + FMA pipes) x 2070 MHz.
 ALU_PEAK_ADDS = 152 * 128 * 2070e6
+# DRAM bytes (read + write) of the four dedispersion launches of one full 131072-sample chunk
+# window of the 4096-channel workload, from one ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_dedisp_tiled_mid_4096ch.md).
+DEDISP_DRAM_BYTES_PER_FULL_CHUNK = 1.313e9 + 0.800e9 + 0.391e9 + 0.201e9
 
 
 def dist_info():
@@ -423,6 +427,70 @@ def batch_workload(args):
     return 0
 
 
+def ooc_workload(args):
+    """The out-of-core shape: 8192 channels over 1000-1500 MHz, 50 us, DM 0-3000 with x1..x16
+    decimation (6050 trials, overlap ~138k samples), 2^19-sample chunks over 4 streams, input in
+    pageable host memory. One step = --ooc-chunks chunks of one continuing stream (a pool of two
+    distinct seeded chunks, reused). Three ways in: pageable through the pinned staging threads
+    (Sec. 2.1; the headline), pageable through the driver, and pinned host memory."""
+    import torch
+
+    import paper_2101_00941_gb300 as dd
+    torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    dd.build()
+    L = 1 << 19
+    w = configs.out_of_core(nsamp=2 * L)
+    w.chunk_len, w.n_streams = L, 4
+    x = np.empty((2 * L, w.nchans), dtype=np.uint8)  # pageable
+    w.generate(pulse_offsets(w), out=x)
+    pool = [x[:L], x[L:]]
+    nchunks = args.ooc_chunks
+    per_chunk = sum(r.n_trials * (L // r.decimation) for r in w.ranges)  # full windows
+    res = {}
+    for mode in ("staged", "driver", "pinned"):
+        plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=w.n_streams,
+                       max_width=max(w.widths), device=dev,
+                       staging_threads=4 if mode == "staged" else 0)
+        src = [torch.from_numpy(c).pin_memory() for c in pool] if mode == "pinned" else pool
+        chunks = [src[k % 2] for k in range(nchunks)]
+        # the first chunk of the stream fills the overlap; it runs before the timed steps
+        plan.run(chunks[0], L)
+        plan.search(w.widths, w.threshold)
+        plan.sync()
+        with ClockSampler(dev) as clk:
+            ms, ncand, launches, _, _ = time_steps(plan, chunks, w, args.steps, args.warmup,
+                                                   lambda: None)
+        plan.close()
+        del src
+        res[mode] = {"value": per_chunk * nchunks * args.steps / (ms * 1e-3),
+                     "ms_per_step": ms / args.steps, "candidates_per_step": ncand / args.steps,
+                     "real_time_factor": nchunks * L * w.tsamp / (ms * 1e-3 / args.steps),
+                     "gpu_launches": launches, "clocks": clk.summary()}
+    head = res["staged"]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32",
+        "data": "synthetic",
+        "config": {"workload": "ooc_8192ch_2e19_chunks", "nchans": w.nchans, "tsamp_us": 50.0,
+                   "trials": w.n_trials, "chunk_len": L, "chunks_per_step": nchunks,
+                   "n_streams": w.n_streams, "staging_threads": 4,
+                   "ranges": [[r.dm_start, r.dm_step, r.n_trials, r.decimation] for r in w.ranges],
+                   "input": "pageable host memory, two 4.3 GB chunks reused",
+                   "h2d_bytes_per_step": nchunks * L * w.nchans},
+        "real_time_factor": head["real_time_factor"],
+        "gpu_launches": head["gpu_launches"],
+        "candidates_per_step": head["candidates_per_step"],
+        "clocks": head["clocks"],
+        "pageable_through_driver": {k: res["driver"][k] for k in ("value", "ms_per_step",
+                                                                  "real_time_factor")},
+        "pinned_host": {k: res["pinned"][k] for k in ("value", "ms_per_step", "real_time_factor")},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main(args):
     import torch
 
@@ -471,6 +539,11 @@ def main(args):
     e2e = total_outs / (ms_e2e * 1e-3)
     adds_per_launch = adds_per_pass(w, O) * args.steps / max(dd_n, 1)
     achieved = adds_per_launch / (dd_ms * 1e-3 / max(dd_n, 1)) if dd_ms > 0 else None
+    # DRAM traffic per launch, averaged like `achieved`: the captured per-chunk bytes scaled by
+    # the step's summed chunk windows (N - O samples); only for the captured configuration
+    traffic = None
+    if (w.nchans, L, tuple(w.ranges)) == (4096, 1 << 17, tuple(configs.MID_RANGES)) and dd_n:
+        traffic = (DEDISP_DRAM_BYTES_PER_FULL_CHUNK * (w.nsamp - O) / L * args.steps / dd_n)
     obs = w.nsamp * w.tsamp
     if rank != 0:
         return 0
@@ -493,7 +566,8 @@ def main(args):
         "gpu_launches": launches,
         "candidates_per_step": ncand / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_ADDS, "unit": "adds/s",
-                     "frac": (achieved / ALU_PEAK_ADDS) if achieved else None, "traffic": None,
+                     "frac": (achieved / ALU_PEAK_ADDS) if achieved else None,
+                     "traffic": traffic, "traffic_unit": "bytes per launch",
                      "kernel": "dedispersion", "launches_timed": dd_n,
                      "peak_note": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)"},
         "clocks": clk.summary(),
@@ -514,7 +588,9 @@ if __name__ == "__main__":
     ap.add_argument("--nsamp", type=int, default=1 << 20,
                     help="samples per beam (a multiple of 2^17; smaller only for profiler captures)")
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the chunks rotate over")
-    ap.add_argument("--workload", choices=["mid", "serve", "batch"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "serve", "batch", "ooc"], default="mid")
+    ap.add_argument("--ooc-chunks", type=int, default=6,
+                    help="ooc: 2^19-sample chunks per step")
     ap.add_argument("--batch-scale", type=int, default=1,
                     help="batch: divide every beam's length by this (profiling only)")
     ap.add_argument("--beams", type=int, default=16, help="serve: beams")
@@ -527,4 +603,6 @@ if __name__ == "__main__":
         sys.exit(main_reference(a))
     if a.workload == "serve":
         sys.exit(serve_workload(a))
+    if a.workload == "ooc":
+        sys.exit(ooc_workload(a))
     sys.exit(batch_workload(a) if a.workload == "batch" else main(a))

@@ -297,13 +297,6 @@ __device__ __forceinline__ double u128_to_f64(unsigned long long hi, unsigned lo
 constexpr int kSpsThreads = 256;
 constexpr int kSpsSeg = 1024;  // window samples per pass
 
-// Largest value of v over the block of B lanes holding `lane` (B a power of two <= 32).
-__device__ __forceinline__ uint32_t block_max(uint32_t v, int B) {
-  if (B == 32) return __reduce_max_sync(0xffffffffu, v);
-  for (int o = B >> 1; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 // Exact argmax over the block: largest v among valid lanes, ties to the lowest lane. Returns
 // -1 when the block has no valid lane; `off` = lane offset within the block.
 __device__ __forceinline__ int block_argmax(uint32_t v, bool valid, int B, int lane, int& off) {
@@ -319,13 +312,13 @@ __device__ __forceinline__ int block_argmax(uint32_t v, bool valid, int B, int l
 
 // One CTA per trial. Each pass covers kSpsSeg window samples plus `hist` samples before them:
 // a uint32 prefix sum in shared memory gives every boxcar exactly (boxcar sums are < 2^31, so
-// the difference of two wrapped prefixes is exact). Per block of B samples and per width the
-// block maximum of the boxcar sum is compared with an integer bound below which the SNR cannot
-// reach the threshold; only blocks that pass run the exact argmax and the FP64 SNR.
+// the difference of two wrapped prefixes is exact). Every boxcar sum is compared with an
+// integer bound per width below which the SNR cannot reach the threshold; only warps where
+// some boxcar passes (i.e. some block's maximum passes) run the exact argmax and the FP64 SNR.
 __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
   extern __shared__ uint32_t P[];  // [1 + hist + kSpsSeg]: P[0] = 0, P[1+u] = sum_{k<=u} mod 2^32
   __shared__ double den[kMaxWidths];
-  __shared__ long long bthr[kMaxWidths];
+  __shared__ uint32_t bthr[kMaxWidths];
   __shared__ uint32_t warp_tot[kSpsThreads / 32];
 
   const int32_t i = blockIdx.x;
@@ -352,7 +345,9 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
     // so that rounding in this estimate can never reject a block the exact test accepts
     const double t = ((double)w * (double)s1 + thr * den[tid]) / (double)n;
     const double tl = t - 2.0 - 1e-9 * fabs(t);
-    bthr[tid] = tl < -4e18 ? -(1ll << 62) : (tl > 4e18 ? (1ll << 62) : (long long)floor(tl));
+    // as a uint32 bound on boxcar sums (< 2^31): at or below 0 every sum passes, above
+    // 2^32 - 1 none does
+    bthr[tid] = tl <= 0.0 ? 0u : (tl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(tl));
   }
   const int H = a.hist;
   const int span = H + kSpsSeg;
@@ -391,7 +386,7 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
       if (e < E) P[1 + tid * E + e] = excl + vals[e];
     __syncthreads();
 
-    // ---- boxcars: block maxima against the integer bounds; exact path only where needed
+    // ---- boxcars against the integer bounds; exact path only where needed
     for (int e = 0; e < kSpsSeg / kSpsThreads; ++e) {
       const long long j = seg0 + e * kSpsThreads + tid;  // window sample
       const int u = H + e * kSpsThreads + tid;           // its entry in P (before the +1)
@@ -402,9 +397,7 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
         if (k < a.nw) {
           const int w = a.wd[k];
           const bool valid = (j < n) && (j >= w - 1);
-          const uint32_t bw = valid ? pj - P[1 + u - w] : 0u;
-          const uint32_t mx = block_max(bw, B);
-          maybe |= (long long)mx >= bthr[k];
+          maybe |= valid && pj - P[1 + u - w] >= bthr[k];
         }
       }
       if (!__any_sync(0xffffffffu, maybe)) continue;
