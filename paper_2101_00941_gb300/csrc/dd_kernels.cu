@@ -295,7 +295,8 @@ __device__ __forceinline__ double u128_to_f64(unsigned long long hi, unsigned lo
 }
 
 constexpr int kSpsThreads = 256;
-constexpr int kSpsSeg = 1024;  // window samples per pass
+constexpr int kSpsSeg = kSpsThreads * 16;         // window samples per pass (16 per thread)
+constexpr int kSpsPad = 3;                        // aligns P[1 + hist + 4k] to 16 bytes
 
 // Exact argmax over the block: largest v among valid lanes, ties to the lowest lane. Returns
 // -1 when the block has no valid lane; `off` = lane offset within the block.
@@ -310,13 +311,33 @@ __device__ __forceinline__ int block_argmax(uint32_t v, bool valid, int B, int l
   return key ? (int)(key >> 32) : -1;
 }
 
-// One CTA per trial. Each pass covers kSpsSeg window samples plus `hist` samples before them:
-// a uint32 prefix sum in shared memory gives every boxcar exactly (boxcar sums are < 2^31, so
-// the difference of two wrapped prefixes is exact). Every boxcar sum is compared with an
-// integer bound per width below which the SNR cannot reach the threshold; only warps where
-// some boxcar passes (i.e. some block's maximum passes) run the exact argmax and the FP64 SNR.
+// Prefix sums through window samples q - w .. q + 3 - w of the pass, i.e. entries
+// P[idx - w .. idx - w + 3] with idx 16-byte aligned: one aligned 16-byte load when w is a
+// multiple of 4, else two, from which the four entries are picked (w is the same in every lane,
+// so the pick is a uniform branch). Lanes take consecutive 16-byte units: no bank conflicts.
+__device__ __forceinline__ uint4 prefix4(const uint32_t* P, int idx, int w) {
+  const int m = (-w) & 3;
+  const uint4* q = reinterpret_cast<const uint4*>(P + idx - w - m);
+  const uint4 a = q[0];
+  if (m == 0) return a;
+  const uint4 b = q[1];
+  if (m == 1) return make_uint4(a.y, a.z, a.w, b.x);
+  if (m == 2) return make_uint4(a.z, a.w, b.x, b.y);
+  return make_uint4(a.w, b.x, b.y, b.z);
+}
+
+// One CTA per trial; passes of kSpsSeg window samples. Warp v owns pass samples
+// 512v .. 512v + 511, lane l the 4-sample chunks 512v + 128g + 4l (g = 0..3). P holds uint32
+// prefix sums of the pass and of the H samples before it (entry 1 + H + q = sum through window
+// sample seg0 + q; the sums wrap, but every boxcar sum is < 2^31, so the difference of two
+// prefixes is exact). The history part is carried over from the previous pass in shared memory.
+// Every boxcar sum is compared with an integer bound per width below which the SNR cannot reach
+// the threshold; a 32-sample group where one passes is searched exactly by its warp (lane =
+// sample): per width the group's largest boxcar sum (earliest sample) per peak block, then the
+// FP64 SNRs in the oracle's evaluation order.
 __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
-  extern __shared__ uint32_t P[];  // [1 + hist + kSpsSeg]: P[0] = 0, P[1+u] = sum_{k<=u} mod 2^32
+  extern __shared__ __align__(16) uint32_t Ps[];
+  uint32_t* P = Ps + kSpsPad;  // [1 + hist + kSpsSeg]
   __shared__ double den[kMaxWidths];
   __shared__ uint32_t bthr[kMaxWidths];
   __shared__ uint32_t warp_tot[kSpsThreads / 32];
@@ -342,113 +363,154 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
     const int w = a.wd[tid];
     den[tid] = sqrt((double)w) * sq;
     // SNR >= thr  <=>  B >= (w*S1 + thr*den) / n; the bound keeps a margin of 2 + 1e-9 relative
-    // so that rounding in this estimate can never reject a block the exact test accepts
+    // so that rounding in this estimate can never reject a block the exact test accepts. As a
+    // uint32 bound on boxcar sums (< 2^31): at or below 0 every sum passes, above 2^32 - 1 none.
     const double t = ((double)w * (double)s1 + thr * den[tid]) / (double)n;
     const double tl = t - 2.0 - 1e-9 * fabs(t);
-    // as a uint32 bound on boxcar sums (< 2^31): at or below 0 every sum passes, above
-    // 2^32 - 1 none does
     bthr[tid] = tl <= 0.0 ? 0u : (tl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(tl));
   }
   const int H = a.hist;
-  const int span = H + kSpsSeg;
-  const int E = span / kSpsThreads;  // entries per thread in the scan (span % 256 == 0)
+  const int nw = a.nw;
+  const int wmax = a.wd[nw - 1];
   const int32_t* yi = a.y + (int64_t)i * a.stride;
+  const bool vec = (reinterpret_cast<uintptr_t>(yi) & 15) == 0;
   const int B = a.block;
-  if (tid == 0) P[0] = 0;
+  const int q0 = wid * 512 + 4 * lane;  // pass sample of this lane's chunk g = 0
+  // samples before the window are zero: the history of the first pass is all zero
+  for (int k = tid; k <= H; k += kSpsThreads) P[k] = 0;
 
   for (long long seg0 = 0; seg0 < n; seg0 += kSpsSeg) {
-    // ---- prefix sums of y[seg0-H .. seg0+kSpsSeg), zero outside the window
-    uint32_t run = 0;
-    uint32_t vals[8];
-    const long long base = seg0 - H + (long long)tid * E;
+    // ---- this lane's four chunks (zero past the window) and their prefix sums
+    uint32_t v[4][4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      if (e < E) {
-        const long long k = base + e;
-        run += (k >= 0 && k < n) ? (uint32_t)yi[k] : 0u;
-        vals[e] = run;
+    for (int g = 0; g < 4; ++g) {
+      const long long j = seg0 + q0 + 128 * g;
+      if (vec && j + 4 <= n) {
+        const int4 t = __ldg(reinterpret_cast<const int4*>(yi + j));
+        v[g][0] = (uint32_t)t.x;
+        v[g][1] = (uint32_t)t.y;
+        v[g][2] = (uint32_t)t.z;
+        v[g][3] = (uint32_t)t.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[g][e] = (j + e < n) ? (uint32_t)__ldg(yi + j + e) : 0u;
       }
     }
-    uint32_t incl = run;
+    uint32_t run = 0;  // sum of this warp's chunks before the current one (lanes, then g)
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += o;
+    for (int g = 0; g < 4; ++g) {
+      v[g][1] += v[g][0];
+      v[g][2] += v[g][1];
+      v[g][3] += v[g][2];
+      uint32_t incl = v[g][3];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+      }
+      const uint32_t pre = run + incl - v[g][3];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[g][e] += pre;
+      run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    __syncthreads();  // previous pass finished reading P
-    if (lane == 31) warp_tot[wid] = incl;
-    __syncthreads();
-    uint32_t woff = 0;
-    for (int k = 0; k < wid; ++k) woff += warp_tot[k];
-    const uint32_t excl = woff + incl - run;
+    if (lane == 0) warp_tot[wid] = run;
+    __syncthreads();  // warp totals; the history entries P[0 .. H] of this pass
+    uint32_t base = P[H];  // sum through the sample before the pass
+    for (int k = 0; k < wid; ++k) base += warp_tot[k];
 #pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if (e < E) P[1 + tid * E + e] = excl + vals[e];
-    __syncthreads();
+    for (int g = 0; g < 4; ++g) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[g][e] += base;  // now prefix sums through each sample
+      *reinterpret_cast<uint4*>(P + 1 + H + q0 + 128 * g) =
+          make_uint4(v[g][0], v[g][1], v[g][2], v[g][3]);
+    }
+    __syncthreads();  // the pass's prefix sums
 
-    // ---- boxcars against the integer bounds; exact path only where needed
-    for (int e = 0; e < kSpsSeg / kSpsThreads; ++e) {
-      const long long j = seg0 + e * kSpsThreads + tid;  // window sample
-      const int u = H + e * kSpsThreads + tid;           // its entry in P (before the +1)
-      const uint32_t pj = P[1 + u];
-      bool maybe = false;
+    // ---- filter: every boxcar sum of this lane's samples against the bounds
+    const long long wj0 = seg0 + wid * 512;  // the warp's first sample
+    const bool interior = wj0 >= wmax - 1 && wj0 + 512 <= n;  // every (sample, width) valid
+    unsigned groups = 0;  // 32-sample groups of the warp's 512 samples with a passing sum
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int idx = 1 + H + q0 + 128 * g;  // entry of this chunk's first sample
+      const long long j = seg0 + q0 + 128 * g;
+      bool hot = false;
 #pragma unroll
       for (int k = 0; k < kMaxWidths; ++k) {
-        if (k < a.nw) {
-          const int w = a.wd[k];
-          const bool valid = (j < n) && (j >= w - 1);
-          maybe |= valid && pj - P[1 + u - w] >= bthr[k];
+        if (k >= nw) break;
+        const int w = a.wd[k];
+        const uint4 st = prefix4(P, idx, w);
+        const uint32_t b0 = v[g][0] - st.x, b1 = v[g][1] - st.y;
+        const uint32_t b2 = v[g][2] - st.z, b3 = v[g][3] - st.w;
+        const uint32_t t = bthr[k];
+        if (interior) {
+          hot |= (b0 >= t) | (b1 >= t) | (b2 >= t) | (b3 >= t);
+        } else {
+          hot |= (j < n && j >= w - 1 && b0 >= t) | (j + 1 < n && j + 1 >= w - 1 && b1 >= t) |
+                 (j + 2 < n && j + 2 >= w - 1 && b2 >= t) | (j + 3 < n && j + 3 >= w - 1 && b3 >= t);
         }
       }
-      if (!__any_sync(0xffffffffu, maybe)) continue;
-      // exact: per width the block's largest boxcar (earliest sample), then the FP64 SNRs in
-      // the oracle's evaluation order; the block leader decides and emits
-      const bool leader = (tid & (B - 1)) == 0;
+      // lanes 8c .. 8c + 7 of chunk row g cover the warp's 32-sample group 4g + c
+      const unsigned hm = __ballot_sync(0xffffffffu, hot);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) groups |= ((hm >> (8 * c)) & 0xFFu) ? (1u << (4 * g + c)) : 0u;
+    }
+
+    // ---- exact search of the hot groups, lane = sample
+    while (groups) {
+      const int c = __ffs(groups) - 1;
+      groups &= groups - 1;
+      const int q = wid * 512 + c * 32 + lane;  // pass sample
+      const long long j = seg0 + q;
+      const uint32_t pj = P[1 + H + q];
+      const bool leader = (lane & (B - 1)) == 0;
       double bs = 0.0;
       long long bj = 0;
       int bwid = 0;
       bool have = false;
-#pragma unroll
-      for (int k = 0; k < kMaxWidths; ++k) {
-        if (k < a.nw) {
-          const int w = a.wd[k];
-          const bool valid = (j < n) && (j >= w - 1);
-          const uint32_t bw = valid ? pj - P[1 + u - w] : 0u;
-          int off;
-          const int best = block_argmax(bw, valid, B, lane, off);
-          if (leader && best >= 0) {
-            const long long num = n * (long long)best - (long long)w * s1;
-            const double snr = (double)num / den[k];
-            const long long jk = j + off;  // the leader holds the block's first sample
-            if (!have || snr > bs || (snr == bs && jk < bj)) {
-              have = true;
-              bs = snr;
-              bj = jk;
-              bwid = w;
-            }
+      for (int k = 0; k < nw; ++k) {
+        const int w = a.wd[k];
+        const bool valid = (j < n) && (j >= w - 1);
+        const uint32_t bw = valid ? pj - P[1 + H + q - w] : 0u;
+        int off;
+        const int best = block_argmax(bw, valid, B, lane, off);
+        if (leader && best >= 0) {
+          const long long num = n * (long long)best - (long long)w * s1;
+          const double snr = (double)num / den[k];
+          const long long jk = j + off;  // the leader holds the block's first sample
+          if (!have || snr > bs || (snr == bs && jk < bj)) {
+            have = true;
+            bs = snr;
+            bj = jk;
+            bwid = w;
           }
         }
       }
       if (leader && have && bs >= thr) {
         const unsigned long long idx = atomicAdd(a.count, 1ull);
         if ((long long)idx < a.cap) {
-          dd_cand_t c;
-          c.trial = i;
-          c.range = a.range;
-          c.t_start = (a.J0 + bj - bwid + 1) * (long long)a.d;
-          c.width = bwid * a.d;
-          c.pad = 0;
-          c.snr = bs;
-          a.cands[idx] = c;
+          dd_cand_t cd;
+          cd.trial = i;
+          cd.range = a.range;
+          cd.t_start = (a.J0 + bj - bwid + 1) * (long long)a.d;
+          cd.width = bwid * a.d;
+          cd.pad = 0;
+          cd.snr = bs;
+          a.cands[idx] = cd;
         }
       }
     }
+    __syncthreads();  // every read of this pass's P is done
+    // the last H + 1 entries become the next pass's history (P[kSpsSeg] = sum before it)
+    for (int k = tid; k <= H; k += kSpsThreads) P[k] = P[kSpsSeg + k];
   }
 }
 
 cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st) {
   if (a.n <= 0 || a.n_trials <= 0 || a.nw <= 0) return cudaSuccess;
-  const size_t smem = sizeof(uint32_t) * (size_t)(1 + a.hist + kSpsSeg);
+  if (a.hist < 0 || a.hist % 4 || a.hist + 1 > kSpsSeg || a.block < 1 || a.block > 32)
+    return cudaErrorInvalidValue;
+  const size_t smem = sizeof(uint32_t) * (size_t)(kSpsPad + 1 + a.hist + kSpsSeg);
   k_sps<<<a.n_trials, kSpsThreads, smem, st>>>(a);
   return cudaGetLastError();
 }

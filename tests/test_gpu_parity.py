@@ -40,12 +40,12 @@ def _as_input(part, kind):
 
 
 def run_gpu(w, x, chunk_sizes, n_streams, kind="device", flags=0, want_series=True,
-            chunk_len=None, trials=None):
+            chunk_len=None, trials=None, block=32):
     ranges = w.ranges_array()
     L = chunk_len or int(-(-max(chunk_sizes) // 256) * 256)
     staging = 4 if kind == "staged" else 0
     plan = dd.Plan(w.freqs(), w.tsamp, ranges, L, n_streams=n_streams, max_width=max(w.widths),
-                   peak_block=32, flags=flags, staging_threads=staging)
+                   peak_block=block, flags=flags, staging_threads=staging)
     out = []
     T = 0
     try:
@@ -71,10 +71,11 @@ def run_gpu(w, x, chunk_sizes, n_streams, kind="device", flags=0, want_series=Tr
     return out, O, shifts
 
 
-def check(w, x, chunk_sizes, n_streams, kind="device", trials=None, flags=0):
+def check(w, x, chunk_sizes, n_streams, kind="device", trials=None, flags=0, block=32):
     ranges = w.ranges_array()
-    gpu, O, shifts = run_gpu(w, x, chunk_sizes, n_streams, kind, trials=trials, flags=flags)
-    ref = oracle.run(x, w.freqs(), w.tsamp, ranges, w.widths, w.threshold, 32, chunk_sizes,
+    gpu, O, shifts = run_gpu(w, x, chunk_sizes, n_streams, kind, trials=trials, flags=flags,
+                             block=block)
+    ref = oracle.run(x, w.freqs(), w.tsamp, ranges, w.widths, w.threshold, block, chunk_sizes,
                      trials=trials)
     assert O == ref["O"]
     np.testing.assert_array_equal(shifts, np.concatenate(ref["tables"]))
@@ -95,7 +96,7 @@ def check(w, x, chunk_sizes, n_streams, kind="device", trials=None, flags=0):
         J0_of = lambda r, per=per: per[r]["J0"]
         tr_index = lambda r: {int(t): i for i, t in enumerate(per[r]["trials"])}
         series_of = lambda r, t, per=per: per[r]["series"][tr_index(r)[t]]
-        nmatch += compare_candidates(got, want, w.threshold, 32, series_of, J0_of, d_of)
+        nmatch += compare_candidates(got, want, w.threshold, block, series_of, J0_of, d_of)
     return nmatch
 
 
@@ -192,6 +193,16 @@ def test_tiled_kernel_full_parity(sizes, n_streams):
     w = _tiled_regime()
     x = w.generate(_arrivals(w))
     assert check(w, x[:sum(sizes)], sizes, n_streams) > 0
+
+
+@pytest.mark.parametrize("block", [1, 8])
+def test_search_peak_blocks_and_odd_widths(block):
+    """Peak blocks smaller than a warp, and boxcar widths that are not powers of two (3, 6, 12,
+    24, 100 original samples: decimated widths 1 .. 100 with every residue mod 4)."""
+    w = _tiled_regime(nsamp=1 << 14)
+    w.widths = (1, 3, 6, 12, 24, 100)
+    x = w.generate(_arrivals(w))
+    assert check(w, x, [4096] * 4, 2, block=block) > 0
 
 
 def test_one_thread_per_output_kernel_matches():
