@@ -34,24 +34,16 @@ struct SpsArgs {
   int32_t n_trials;
   int32_t range;
   int32_t d;
-  int32_t block;           // samples per candidate block (power of two <= 256)
+  int32_t block;           // samples per candidate block (power of two <= 32)
   int64_t J0;              // global decimated index of window sample 0
   int32_t nw;
-  int32_t hist;            // largest decimated width - 1 rounded up to 32
+  int32_t hist;            // largest decimated width - 1, rounded up to 256
   int32_t wd[kMaxWidths];  // decimated widths, increasing
   float threshold;
   int32_t pad;
   dd_cand_t* cands;
   unsigned long long* count;
   int64_t cap;
-};
-
-// Work list entry of the tiled dedispersion kernel (one CTA).
-struct DedispTile {
-  int32_t range;        // range index
-  int32_t trial0;       // first trial of the tile within the range
-  int32_t ntr;          // trials in the tile (<= kTileTrials)
-  int32_t j0;           // first window sample of the tile
 };
 
 // Per-range geometry of one chunk for the tiled dedispersion kernel.
