@@ -491,6 +491,53 @@ def ooc_workload(args):
     return 0
 
 
+def transfer_workload(args):
+    """The paper's transfer micro-experiment (Sec. 2, Sec. 2.1) on this machine: host-to-device
+    throughput from pageable and from pinned memory, and the cost of allocating pinned memory
+    (first allocation of each size), for 1 MiB .. 4 GiB. Each copy is timed with CUDA events,
+    best of 5 after one warm-up."""
+    import torch
+    torch.cuda.set_device(0)
+    sizes = [1 << 20, 16 << 20, 256 << 20, 1 << 30, 4 << 30]
+    rows = []
+    dst = torch.empty(max(sizes), dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def h2d_gbs(src, nbytes):
+        best = None
+        for k in range(6):
+            torch.cuda.synchronize()
+            e0.record()
+            dst[:nbytes].copy_(src, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if k > 0:
+                best = ms if best is None else min(best, ms)
+        return nbytes / (best * 1e-3) / 1e9
+
+    for nb in sizes:
+        pageable = torch.from_numpy(np.ones(nb, dtype=np.uint8))
+        t0 = time.perf_counter()
+        pinned = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        alloc_ms = 1e3 * (time.perf_counter() - t0)
+        pinned.fill_(1)
+        rows.append({"bytes": nb, "pageable_gbs": h2d_gbs(pageable, nb),
+                     "pinned_gbs": h2d_gbs(pinned, nb), "pinned_alloc_ms": alloc_ms})
+        del pinned, pageable
+    big = rows[-1]
+    line = {
+        "metric": "H2D GB/s from pinned host memory", "value": big["pinned_gbs"], "unit": "GB/s",
+        "n_gpus": 1, "steps": 5, "warmup": 1, "higher_is_better": True, "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "transfer_1MiB-4GiB", "timing": "CUDA events, best of 5",
+                   "allocator": "torch pin_memory (cudaHostAlloc)"},
+        "sizes": rows,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main(args):
     import torch
 
@@ -588,7 +635,8 @@ if __name__ == "__main__":
     ap.add_argument("--nsamp", type=int, default=1 << 20,
                     help="samples per beam (a multiple of 2^17; smaller only for profiler captures)")
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the chunks rotate over")
-    ap.add_argument("--workload", choices=["mid", "serve", "batch", "ooc"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "serve", "batch", "ooc", "transfer"],
+                    default="mid")
     ap.add_argument("--ooc-chunks", type=int, default=6,
                     help="ooc: 2^19-sample chunks per step")
     ap.add_argument("--batch-scale", type=int, default=1,
@@ -605,4 +653,6 @@ if __name__ == "__main__":
         sys.exit(serve_workload(a))
     if a.workload == "ooc":
         sys.exit(ooc_workload(a))
+    if a.workload == "transfer":
+        sys.exit(transfer_workload(a))
     sys.exit(batch_workload(a) if a.workload == "batch" else main(a))

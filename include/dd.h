@@ -334,6 +334,20 @@ int dd_serve_pending(dd_server_t server, int64_t* queued, int32_t* inflight);
  * finish) and release every beam's plan. NULL is a no-op. */
 void dd_serve_destroy(dd_server_t server);
 
+/*
+ * dd_selftest_wait -- failure-detection self-test of the device-side bounded wait. The tiled
+ * dedispersion kernel waits on each stage's copy barrier for at most 2 s (or 2^26 polls); when
+ * that runs out it sets an error bit that dd_candidates reports as DD_ERR_TIMEOUT, waits (again
+ * bounded) for its copies in flight and returns, so the CUDA context stays usable. This call
+ * runs the same wait in one thread on a barrier that nothing completes, on its own stream, and
+ * reports the outcome. It allocates 4 bytes of device memory for the duration of the call.
+ *   device    : CUDA device to run on
+ *   timed_out : receives 1 if the wait ran out and was reported (the designed outcome), else 0
+ *   waited_ms : receives the call's host-measured duration (may be NULL)
+ * Errors: DD_ERR_ARG (NULL timed_out), DD_ERR_NOMEM, DD_ERR_CUDA.
+ */
+int dd_selftest_wait(int32_t device, int32_t* timed_out, double* waited_ms);
+
 /* dd_last_error -- message of the calling thread's last error ("" if none). Library-owned. */
 const char* dd_last_error(void);
 

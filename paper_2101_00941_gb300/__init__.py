@@ -28,7 +28,7 @@ DD_FLAG_DEVICE_INPUT = 4
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
 
-EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
+EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_selftest_wait", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
            "dd_stats", "dd_sps_static", "dd_serve_create", "dd_serve_add_beam", "dd_serve_submit",
            "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_batch_create",
            "dd_batch_run", "dd_batch_wait", "dd_batch_info", "dd_batch_candidates",
@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
         L.dd_plan.argtypes = [vp, i32, f64, vp, i32, P(dd_opts_t), P(vp)]
         L.dd_plan_info.argtypes = [vp, P(i64), P(i32), P(vp)]
         L.dd_plan_kernel.argtypes = [vp, i32, P(i32), P(i32)]
+        L.dd_selftest_wait.argtypes = [i32, P(i32), P(ctypes.c_double)]
         L.dd_run.argtypes = [vp, vp, i64, vp]
         L.dd_series.argtypes = [vp, i32, P(vp), P(i64), P(i64), P(i64)]
         L.sps_run.argtypes = [vp, vp, i32, f32]
@@ -171,6 +172,13 @@ def dd_plan_kernel(plan: int, range_idx: int):
     t, tt = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().dd_plan_kernel(plan, int(range_idx), ctypes.byref(t), ctypes.byref(tt)))
     return t.value, tt.value
+
+
+def dd_selftest_wait(device: int = 0):
+    """(1 if the device-side bounded wait ran out and was reported, host ms) -- see dd.h."""
+    t, ms = ctypes.c_int32(), ctypes.c_double()
+    _check(lib().dd_selftest_wait(int(device), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def dd_run(plan: int, chunk, nsamp: int, cuda_stream: int = 0):

@@ -980,6 +980,31 @@ int dd_candidates(dd_plan_t p, int64_t seq, dd_cand_t* out, int64_t cap, int64_t
   return DD_OK;
 }
 
+int dd_selftest_wait(int32_t device, int32_t* timed_out, double* waited_ms) {
+  if (!timed_out) return fail(DD_ERR_ARG, "timed_out is NULL");
+  *timed_out = 0;
+  DD_CK(cudaSetDevice(device));
+  const auto t0 = std::chrono::steady_clock::now();
+  int32_t* d_err = nullptr;
+  if (cudaMalloc(&d_err, sizeof(int32_t)) != cudaSuccess)
+    return fail(DD_ERR_NOMEM, "self-test: no device memory for the status word");
+  cudaStream_t st = nullptr;
+  int32_t herr = 0;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = ddk::launch_wait_selftest(d_err, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return fail(DD_ERR_CUDA, "self-test: %s", cudaGetErrorString(e));
+  *timed_out = (herr & 1) ? 1 : 0;
+  if (waited_ms)
+    *waited_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                     .count();
+  return DD_OK;
+}
+
 int dd_sync(dd_plan_t p) {
   if (!p) return fail(DD_ERR_ARG, "plan is NULL");
   DD_CK(cudaSetDevice(p->device));

@@ -572,7 +572,24 @@ bool deal_work(StageTab& st, int U) {
   return true;
 }
 
+// Self-test of the bounded wait above: one thread arms a fresh mbarrier that nothing ever
+// completes and waits on it; when the bound runs out it records the error bit, as the tiled
+// kernel does for a copy that never lands.
+__global__ void k_wait_selftest(int32_t* err) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait_bounded(&bar, 0)) atomicOr(err, 1);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(int32_t* err, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err);
+  return cudaGetLastError();
+}
 
 int tiled_tile_samples(int is_u16, int choice) {
   // preferred time tile first, a smaller one when the first does not fit shared memory

@@ -95,6 +95,9 @@ struct TiledPlan {
 int tiled_tile_samples(int is_u16, int choice);
 TiledPlan tiled_plan(const int32_t* shifts, int ntr, int cpad, int decimation, int tt);
 cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
+// One CTA waits, with the tiled kernel's bound, on a barrier nothing completes; sets *err bit 0
+// when the bound runs out.
+cudaError_t launch_wait_selftest(int32_t* err, cudaStream_t st);
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st);
 
 // Tensor map of a channel-major ring (uint8, or uint16 when is_u16) for the tiled kernel's

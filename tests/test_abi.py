@@ -76,6 +76,7 @@ def test_null_handles(lib):
     assert lib.sps_run(None, None, 0, ctypes.c_float(6.0)) == dd.DD_ERR_ARG
     assert lib.dd_sync(None) == dd.DD_ERR_ARG
     assert lib.dd_plan_kernel(None, 0, None, None) == dd.DD_ERR_ARG
+    assert lib.dd_selftest_wait(0, None, None) == dd.DD_ERR_ARG
     lib.dd_plan_destroy(None)
 
 
