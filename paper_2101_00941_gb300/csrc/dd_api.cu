@@ -162,6 +162,7 @@ struct RangeKernel {
   bool tiled = false;
   int tt = 0;
   int nseg = 0;
+  int nstage = 0;
   int row_slot = 0;
   int zcap = 0;
   size_t smem = 0;
@@ -412,13 +413,14 @@ int plan_autotune(dd_plan_s* p) {
         }
         if (cudaMemcpy(k.d_tabs, tp.tabs.data(), tp.tab_bytes, cudaMemcpyHostToDevice) !=
                 cudaSuccess ||
-            ddk::prepare_tiled(u16, tt, tp.smem) != cudaSuccess) {
+            ddk::prepare_tiled(u16, tt, tp.nstage, tp.smem) != cudaSuccess) {
           cudaFree(k.d_tabs);
           rc = fail(DD_ERR_CUDA, "autotune: set-up failed");
           break;
         }
         k.tt = tt;
         k.nseg = tp.nseg;
+        k.nstage = tp.nstage;
         k.row_slot = tp.row_slot;
         k.zcap = tp.zcap;
         k.smem = tp.smem;
@@ -442,6 +444,7 @@ int plan_autotune(dd_plan_s* p) {
       A.cpad = p->Cp;
       A.row_slot = k.row_slot;
       A.zcap = k.zcap;
+      A.nstage = k.nstage;
       A.tabs = k.d_tabs;
       A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
       float ms = 0;
@@ -649,7 +652,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
           }
           cudaError_t e2 = cudaMemcpy(k.d_tabs, tp.tabs.data(), tp.tab_bytes,
                                       cudaMemcpyHostToDevice);
-          if (e2 == cudaSuccess) e2 = ddk::prepare_tiled(u16, tt, tp.smem);
+          if (e2 == cudaSuccess) e2 = ddk::prepare_tiled(u16, tt, tp.nstage, tp.smem);
           if (e2 != cudaSuccess) {
             free_plan(p);
             return fail(DD_ERR_CUDA, "tiled kernel set-up: %s", cudaGetErrorString(e2));
@@ -657,6 +660,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
           k.tiled = true;
           k.tt = tt;
           k.nseg = tp.nseg;
+          k.nstage = tp.nstage;
           k.row_slot = tp.row_slot;
           k.zcap = tp.zcap;
           k.smem = tp.smem;
@@ -848,6 +852,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       A.cpad = p->Cp;
       A.row_slot = K.row_slot;
       A.zcap = K.zcap;
+      A.nstage = K.nstage;
       A.tabs = K.d_tabs;
       A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
       DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, st));

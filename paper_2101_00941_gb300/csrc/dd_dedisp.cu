@@ -14,12 +14,13 @@
 //     warps; the kernel never searches for them.
 //   * TMA brings each stage's 16 channel rows (one 3-D tensor copy: every row from the same
 //     128-byte segment on, so each lands contiguous) and its class table into shared memory
-//     kNStage stages ahead; completion is tracked by mbarriers with bounded waits.
+//     NS - 1 stages ahead (NS = 4 staging buffers, or 3 where 4 do not fit shared memory);
+//     completion is tracked by mbarriers with bounded waits.
 //   * The main loop adds one pattern word per (trial, sample) with one DP2A: one 32-bit
 //     shared-memory load per eight channel-adds, for uint8 and uint16 (decimated) data alike.
 //
 // Software pipeline, one __syncthreads per stage s:
-//     TMA for stage s+kNStage-1 | build the words of stage s+1 | accumulate stage s
+//     TMA for stage s+NS-1 | build the words of stage s+1 | accumulate stage s
 // Words are built from 32-bit loads and funnel shifts; the four-channel sums are formed in SWAR
 // lanes (bytes split into 16-bit lanes for uint8 data). Where each class's channel rows start in
 // a stage buffer (row word and funnel shift) depends on where the stage's copy starts, so the
@@ -46,10 +47,11 @@ constexpr int kTPW = kTileTrials / kWarps;  // trials per warp
 constexpr int kG = 8;                       // channels per group (one pattern word)
 constexpr int kNG = 2;                      // groups per stage
 constexpr int kRows = kG * kNG;             // channel rows per stage
-constexpr int kNStage = 4;                  // staging buffers (rows + class table)
+constexpr int kMaxNStage = 4;               // staging buffers (rows + class table), at most
 constexpr int kMaxCls = 16;                 // classes per group
 constexpr int kMaxWork = 8;                 // build ranges per warp and stage
 constexpr int kSegBytes = 128;              // inner extent of a staged-row copy (tensor map)
+constexpr size_t kSmemLimit = 220 * 1024;   // dynamic shared memory a CTA may plan for
 
 // One delay class: its channels' first staged sample relative to the tile's first trial
 // (rel), and its words in the stage's pattern-word region.
@@ -94,19 +96,20 @@ struct SmemLayout {
   size_t raw, z, tab, addr, mbar, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot, int zcap) {
+__host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot, int zcap,
+                                                  int nst) {
   SmemLayout L;
   size_t off = 0;
   L.raw = off;
-  off = align16(off + (size_t)kNStage * kRows * row_slot * es);
+  off = align16(off + (size_t)nst * kRows * row_slot * es);
   L.z = off;
   off = align16(off + (size_t)2 * zcap * zes);
   L.tab = off;
-  off = align16(off + sizeof(StageTab) * kNStage);
+  off = align16(off + sizeof(StageTab) * nst);
   L.addr = off;
   off = align16(off + sizeof(AddrTab) * 2);
   L.mbar = off;
-  off = align16(off + sizeof(unsigned long long) * kNStage);
+  off = align16(off + sizeof(unsigned long long) * nst);
   L.total = off;
   return L;
 }
@@ -358,12 +361,12 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
   }
 }
 
-template <typename T, int TT>
+template <typename T, int TT, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_dedisp_tiled(const __grid_constant__ TiledArgs a) {
   constexpr int KT = TT / 32;
   extern __shared__ __align__(1024) unsigned char smem[];  // tensor copies land 128-aligned
-  const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap);
+  const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap, NS);
   T* raw = reinterpret_cast<T*>(smem + SL.raw);
   uint32_t* Zbuf = reinterpret_cast<uint32_t*>(smem + SL.z);
   StageTab* tab = reinterpret_cast<StageTab*>(smem + SL.tab);
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const size_t stage_elems = (size_t)kRows * a.row_slot;
 
   if (tid == 0) {
-    for (int s = 0; s < kNStage; ++s) mbar_init(&mbar[s], 1);
+    for (int s = 0; s < NS; ++s) mbar_init(&mbar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -395,15 +398,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid < kAddrEntries) ain = addr_inputs(a, 2, nstages, ngroups, trial0, tid);
   }
   __syncthreads();
-  // stages whose copies have been issued: kNStage in the prologue, then one per iteration s >= 1
+  // stages whose copies have been issued: NS in the prologue, then one per iteration s >= 1
   // (the same count in every thread)
-  int issued = min(kNStage, nstages);
+  int issued = min(NS, nstages);
   int32_t xmin_next = 0;  // first delay of the next stage to issue (issuing thread)
   if (tid == kThreads - 32) {
-    for (int s = 0; s < kNStage && s < nstages; ++s)
+    for (int s = 0; s < NS && s < nstages; ++s)
       issue_stage<T>(a, s, nstages, raw + (size_t)s * stage_elems, &tab[s], &mbar[s],
                      stage_xmin(a, s, nstages), j0);
-    xmin_next = stage_xmin(a, kNStage, nstages);
+    xmin_next = stage_xmin(a, NS, nstages);
   }
   bool ok0 = mbar_wait_bounded(&mbar[0], 0);
   if (ok0) build_stage<T>(tab[0], atab[0], smem_addr(raw), Zbuf, warp, lane);
@@ -418,11 +421,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   for (int s = 0; s < nstages && !aborted; ++s) {
     const int ng = min(kNG, ngroups - s * kNG);
-    // (1) TMA for stage s + kNStage - 1 into the buffers stage s - 1 used (its words were built
+    // (1) TMA for stage s + NS - 1 into the buffers stage s - 1 used (its words were built
     //     during stage s - 2 and its table last read by the accumulation of stage s - 1)
-    if (s >= 1 && s + kNStage - 1 < nstages) {
-      const int s2 = s + kNStage - 1;
-      const int b2 = s2 % kNStage;
+    if (s >= 1 && s + NS - 1 < nstages) {
+      const int s2 = s + NS - 1;
+      const int b2 = s2 % NS;
       if (tid == kThreads - 32) {
         issue_stage<T>(a, s2, nstages, raw + (size_t)b2 * stage_elems, &tab[b2], &mbar[b2],
                        xmin_next, j0);
@@ -438,15 +441,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     // (2) pattern words of stage s + 1
     bool ok = true;
     if (s + 1 < nstages) {
-      const int b1 = (s + 1) % kNStage;
-      ok = mbar_wait_bounded(&mbar[b1], (uint32_t)(((s + 1) / kNStage) & 1));
+      const int b1 = (s + 1) % NS;
+      ok = mbar_wait_bounded(&mbar[b1], (uint32_t)(((s + 1) / NS) & 1));
       if (ok)
         build_stage<T>(tab[b1], atab[(s + 1) & 1], smem_addr(raw + (size_t)b1 * stage_elems),
                        Zbuf + (size_t)((s + 1) & 1) * a.zcap, warp, lane);
     }
     // (3) accumulate stage s
     {
-      const StageTab& tc = tab[s % kNStage];
+      const StageTab& tc = tab[s % NS];
       const uint32_t* Zs = Zbuf + (size_t)(s & 1) * a.zcap + lane;
 #pragma unroll
       for (int g = 0; g < kNG; ++g) {
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       atomicOr(a.err, 1);
       // let every copy still in flight land before the CTA's shared memory goes away
       for (int s = s_abort; s < issued; ++s)
-        mbar_wait_bounded(&mbar[s % kNStage], (uint32_t)((s / kNStage) & 1));
+        mbar_wait_bounded(&mbar[s % NS], (uint32_t)((s / NS) & 1));
     }
     return;
   }
@@ -515,18 +518,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <typename T, int TT>
+template <typename T, int TT, int NS>
 cudaError_t launch_tiled_t(const TiledArgs& a, cudaStream_t st) {
-  const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap);
+  const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap, NS);
   dim3 grid((unsigned)((a.n_trials + kTileTrials - 1) / kTileTrials),
             (unsigned)((a.nout + TT - 1) / TT));
-  k_dedisp_tiled<T, TT><<<grid, kThreads, SL.total, st>>>(a);
+  k_dedisp_tiled<T, TT, NS><<<grid, kThreads, SL.total, st>>>(a);
   return cudaGetLastError();
 }
 
 // Ranges sharing an instance need different amounts of shared memory, so the instance is
 // allowed the device's opt-in maximum once (a launch still only reserves what it asks for).
-template <typename T, int TT>
+template <typename T, int TT, int NS>
 cudaError_t prepare_t(size_t smem) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -534,8 +537,8 @@ cudaError_t prepare_t(size_t smem) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   if (smem > (size_t)optin) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(k_dedisp_tiled<T, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              optin);
+  return cudaFuncSetAttribute(k_dedisp_tiled<T, TT, NS>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 }  // namespace
@@ -696,20 +699,30 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
   if (P.nseg > 255) return P;
   P.row_slot = P.nseg * SEG;
   P.zcap = (int)((std::max<int64_t>(zcap, 4) + 3) / 4 * 4);
-  P.smem = smem_layout(u16 ? 2 : 1, 4, P.row_slot, P.zcap).total;
   P.tab_bytes = out.size() * sizeof(StageTab);
   P.tabs.resize(P.tab_bytes);
   std::memcpy(P.tabs.data(), out.data(), P.tab_bytes);
   // addressing entries hold byte offsets within a stage buffer as uint16
-  P.ok = P.smem <= 200 * 1024 && (size_t)kRows * P.row_slot * (u16 ? 2 : 1) <= 65535;
+  if ((size_t)kRows * P.row_slot * (u16 ? 2 : 1) > 65535) return P;
+  // as many staging buffers as fit (4, else 3: a copy is then issued two stages ahead)
+  for (int nst = kMaxNStage; nst >= 3 && !P.ok; --nst) {
+    P.nstage = nst;
+    P.smem = smem_layout(u16 ? 2 : 1, 4, P.row_slot, P.zcap, nst).total;
+    P.ok = P.smem <= kSmemLimit;
+  }
   return P;
 }
 
-cudaError_t prepare_tiled(int is_u16, int tt, size_t smem) {
-  if (!is_u16 && tt == 512) return prepare_t<uint8_t, 512>(smem);
-  if (!is_u16 && tt == 256) return prepare_t<uint8_t, 256>(smem);
-  if (is_u16 && tt == 512) return prepare_t<uint16_t, 512>(smem);
-  if (is_u16 && tt == 256) return prepare_t<uint16_t, 256>(smem);
+// Instances: uint8/uint16 data x 512/256-sample tiles x 4/3 staging buffers.
+#define DD_TILED_INSTANCES(X) \
+  X(uint8_t, 0, 512, 4) X(uint8_t, 0, 512, 3) X(uint8_t, 0, 256, 4) X(uint8_t, 0, 256, 3) \
+  X(uint16_t, 1, 512, 4) X(uint16_t, 1, 512, 3) X(uint16_t, 1, 256, 4) X(uint16_t, 1, 256, 3)
+
+cudaError_t prepare_tiled(int is_u16, int tt, int nstage, size_t smem) {
+#define DD_PREPARE(T, U16, TT, NS) \
+  if (is_u16 == U16 && tt == TT && nstage == NS) return prepare_t<T, TT, NS>(smem);
+  DD_TILED_INSTANCES(DD_PREPARE)
+#undef DD_PREPARE
   return cudaErrorInvalidValue;
 }
 
@@ -754,10 +767,10 @@ cudaError_t make_ring_map(CUtensorMap* map, const void* ring, int is_u16, int64_
 
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st) {
   if (a.nout <= 0 || a.n_trials <= 0) return cudaSuccess;
-  if (!is_u16 && tt == 512) return launch_tiled_t<uint8_t, 512>(a, st);
-  if (!is_u16 && tt == 256) return launch_tiled_t<uint8_t, 256>(a, st);
-  if (is_u16 && tt == 512) return launch_tiled_t<uint16_t, 512>(a, st);
-  if (is_u16 && tt == 256) return launch_tiled_t<uint16_t, 256>(a, st);
+#define DD_LAUNCH(T, U16, TT, NS) \
+  if (is_u16 == U16 && tt == TT && a.nstage == NS) return launch_tiled_t<T, TT, NS>(a, st);
+  DD_TILED_INSTANCES(DD_LAUNCH)
+#undef DD_LAUNCH
   return cudaErrorInvalidValue;
 }
 

@@ -74,6 +74,7 @@ struct TiledArgs {
   int32_t cpad;
   int32_t row_slot;        // elements per staged channel row
   int32_t zcap;            // pattern words per stage
+  int32_t nstage;          // staging buffers (3 or 4)
   const uint8_t* tabs;     // delay-class tables of the range, one per (trial tile, stage)
   int32_t* err;            // bit 0: a bounded wait ran out
   CUtensorMap rows;        // the ring as [Cp][xd_stride / seg][seg] (make_ring_map)
@@ -85,6 +86,7 @@ struct TiledPlan {
   bool ok = false;
   int tt = 0;
   int nseg = 0;            // 128-byte segments per staged channel row
+  int nstage = 0;          // staging buffers
   int row_slot = 0;
   int zcap = 0;
   size_t smem = 0;
@@ -94,7 +96,7 @@ struct TiledPlan {
 
 int tiled_tile_samples(int is_u16, int choice);
 TiledPlan tiled_plan(const int32_t* shifts, int ntr, int cpad, int decimation, int tt);
-cudaError_t prepare_tiled(int is_u16, int tt, size_t smem);
+cudaError_t prepare_tiled(int is_u16, int tt, int nstage, size_t smem);
 // One CTA waits, with the tiled kernel's bound, on a barrier nothing completes; sets *err bit 0
 // when the bound runs out.
 cudaError_t launch_wait_selftest(int32_t* err, cudaStream_t st);
