@@ -51,6 +51,17 @@ def dist_info():
     return rank, world, local
 
 
+def rank_max(values, device):
+    """Element-wise max over ranks of per-rank timings (a multi-GPU step lasts as long as its
+    slowest rank); the values unchanged with one process."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def outputs_per_pass(w, O: int) -> int:
     """DM-trial*samples produced from one beam: sum_r n_r * (N - O) / d_r."""
     return sum(r.n_trials * ((w.nsamp - O) // r.decimation) for r in w.ranges)
@@ -577,10 +588,7 @@ def main(args):
                                             lat)
     plan.close()
     if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+        ms, ms_e2e = rank_max([ms, ms_e2e], "cuda")
     total_outs = outs * args.steps * world
     value = total_outs / (ms * 1e-3)
     e2e = total_outs / (ms_e2e * 1e-3)
