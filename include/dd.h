@@ -117,13 +117,17 @@ int dd_plan_info(dd_plan_t plan, int64_t* overlap, int32_t* ntrials, const int32
 
 /*
  * dd_plan_kernel -- which dedispersion kernel range `range` (0-based, plan order) runs on.
- *   tiled        : 1 = the tiled delay-class kernel, 0 = the per-output kernel (chosen when the
- *                  range's delay classes or decimation exceed the tiled kernel's table limits,
- *                  or with DD_FLAG_NAIVE) (may be NULL)
- *   tile_samples : outputs per time tile of the tiled kernel, 0 for the other (may be NULL)
+ *   kind         : DD_KERNEL_TILED (delay classes shared by a 64-trial tile), DD_KERNEL_DIRECT
+ *                  (the fallback where the range's delay classes or decimation exceed the tiled
+ *                  kernel's limits: coarse channels, decimation above x64) or
+ *                  DD_KERNEL_PER_OUTPUT (one thread per output, with DD_FLAG_NAIVE) (may be NULL)
+ *   tile_samples : outputs per time tile of the tiled kernel, 0 for the others (may be NULL)
  * Errors: DD_ERR_ARG (NULL plan, range out of bounds).
  */
-int dd_plan_kernel(dd_plan_t plan, int32_t range, int32_t* tiled, int32_t* tile_samples);
+#define DD_KERNEL_TILED 1
+#define DD_KERNEL_DIRECT 2
+#define DD_KERNEL_PER_OUTPUT 3
+int dd_plan_kernel(dd_plan_t plan, int32_t range, int32_t* kind, int32_t* tile_samples);
 
 /*
  * dd_run -- enqueue the dedispersion of the next time chunk (Sec. 1, Sec. 2.1).

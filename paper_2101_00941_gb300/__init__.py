@@ -20,6 +20,7 @@ DD_ERR_ARG = -1
 DD_ERR_NOMEM = -2
 DD_ERR_CUDA = -3
 DD_ERR_TIMEOUT = -4
+DD_KERNEL_TILED, DD_KERNEL_DIRECT, DD_KERNEL_PER_OUTPUT = 1, 2, 3
 DD_ERR_CAP = -5
 DD_ERR_STATE = -6
 DD_FLAG_TIMING = 1
@@ -168,7 +169,7 @@ def dd_plan_info(plan: int, nchans: int):
 
 
 def dd_plan_kernel(plan: int, range_idx: int):
-    """(1 if range `range_idx` runs on the tiled kernel else 0, its time tile or 0)."""
+    """(kernel kind of range `range_idx`: DD_KERNEL_TILED / _DIRECT / _PER_OUTPUT, tile or 0)."""
     t, tt = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().dd_plan_kernel(plan, int(range_idx), ctypes.byref(t), ctypes.byref(tt)))
     return t.value, tt.value
@@ -246,7 +247,7 @@ class Plan:
         self.seq = -1
 
     def kernel(self, range_idx):
-        """(tiled, tile samples) of one range; see dd_plan_kernel."""
+        """(kernel kind, tile samples) of one range; see dd_plan_kernel."""
         return dd_plan_kernel(self.h, range_idx)
 
     def run(self, chunk, nsamp=None, cuda_stream=0) -> int:

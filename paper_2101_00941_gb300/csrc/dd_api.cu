@@ -754,12 +754,15 @@ int dd_plan_info(dd_plan_t p, int64_t* overlap, int32_t* ntrials, const int32_t*
   return DD_OK;
 }
 
-int dd_plan_kernel(dd_plan_t p, int32_t range, int32_t* tiled, int32_t* tile_samples) {
+int dd_plan_kernel(dd_plan_t p, int32_t range, int32_t* kind, int32_t* tile_samples) {
   if (!p) return fail(DD_ERR_ARG, "plan is NULL");
   if (range < 0 || range >= (int32_t)p->rk.size())
     return fail(DD_ERR_ARG, "range %d out of bounds", (int)range);
-  if (tiled) *tiled = p->rk[range].tiled ? 1 : 0;
-  if (tile_samples) *tile_samples = p->rk[range].tiled ? p->rk[range].tt : 0;
+  const bool tiled = p->rk[range].tiled;
+  if (kind)
+    *kind = tiled ? DD_KERNEL_TILED
+                  : ((p->opts.flags & DD_FLAG_NAIVE) ? DD_KERNEL_PER_OUTPUT : DD_KERNEL_DIRECT);
+  if (tile_samples) *tile_samples = tiled ? p->rk[range].tt : 0;
   return DD_OK;
 }
 
@@ -857,8 +860,10 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
       DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, st));
       p->launches += 1;
-    } else {
+    } else if (p->opts.flags & DD_FLAG_NAIVE) {
       DD_CK(ddk::launch_dedisp_naive(R, p->Cp, st));
+    } else {
+      DD_CK(ddk::launch_dedisp_direct(R, p->Cp, st));
     }
     rc = timing_end(p, st, ts);
     if (rc) return rc;

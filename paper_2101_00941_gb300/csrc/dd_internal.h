@@ -137,6 +137,7 @@ cudaError_t launch_corner_turn(const uint8_t* in, int64_t n, int32_t nchans, uin
 cudaError_t launch_decimate(const void* in, int in_is_u16, int64_t in_stride, uint16_t* out,
                             int64_t out_stride, int32_t cpad, int64_t n_out, cudaStream_t st);
 cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t cpad, cudaStream_t st);
+cudaError_t launch_dedisp_direct(const DedispRange& r, int32_t cpad, cudaStream_t st);
 cudaError_t launch_moments(const int32_t* y, int32_t ntr, int64_t n, int64_t stride, Moments* mom,
                            cudaStream_t st);
 cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st);

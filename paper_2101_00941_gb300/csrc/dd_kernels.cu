@@ -215,6 +215,115 @@ cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t cpad, cudaStream_t
   return cudaGetLastError();
 }
 
+// Direct kernel: the fallback for ranges the tiled kernel cannot take (delay classes beyond
+// its tables, as with coarse channels, or decimation above x64). A CTA of 8 warps owns 16
+// consecutive trials x 512 outputs; a warp takes 2 trials, lane l the 4-sample groups
+// 4l + 128g (g = 0..3) of both. Per channel a lane reads, through the read-only cache, the two
+// aligned 32-bit words holding its 4 samples and funnel-shifts them into place (the shift is
+// the same in every lane of the warp: it depends only on m0 + delay). uint8 samples are added
+// in 16-bit SWAR lanes (even / odd samples), flushed to 32-bit sums every 256 channels
+// (256 x 255 < 2^16); uint16 samples (up to 255 x 256) are added to 32-bit sums directly.
+constexpr int kDirectTrials = 16;
+constexpr int kDirectTile = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dedisp_direct(const T* __restrict__ xd, int64_t stride,
+                                                       int32_t cpad, int64_t m0, int64_t nout,
+                                                       int32_t n_trials,
+                                                       const int32_t* __restrict__ shifts,
+                                                       int32_t* __restrict__ y, int64_t y_stride) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t tbase = blockIdx.x * kDirectTrials + 2 * warp;
+  if (tbase >= n_trials) return;  // whole warp
+  const int ntr = min(2, n_trials - tbase);
+  const int64_t j0 = (int64_t)blockIdx.y * kDirectTile;
+  uint32_t acc[2][4][4];  // [trial][group g][sample e]
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[q][g][e] = 0;
+  const char* base = reinterpret_cast<const char*>(xd);
+  const int64_t row_bytes = stride * (int64_t)sizeof(T);
+  for (int32_t c0 = 0; c0 < cpad; c0 += 256) {
+    uint32_t ev[2][4], od[2][4];  // uint8 path: packed 16-bit sums of samples (0,2) and (1,3)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int g = 0; g < 4; ++g) ev[q][g] = od[q][g] = 0;
+    const int32_t c1 = min(cpad, c0 + 256);
+    for (int32_t c = c0; c < c1; ++c) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q < ntr) {
+          const int64_t s = __ldg(shifts + (int64_t)(tbase + q) * cpad + c);
+          // byte address of this lane's first sample of group 0
+          const int64_t b = (int64_t)c * row_bytes + (m0 + j0 + s + 4 * lane) * (int64_t)sizeof(T);
+          const uint32_t sh = (uint32_t)(b & 3) * 8u;
+          const uint32_t* wp = reinterpret_cast<const uint32_t*>(base + (b & ~(int64_t)3));
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            if (sizeof(T) == 1) {
+              const uint32_t* p = wp + 32 * g;  // 128 samples further per group
+              const uint32_t v = __funnelshift_r(__ldg(p), __ldg(p + 1), sh);
+              ev[q][g] += v & 0x00FF00FFu;
+              od[q][g] += __byte_perm(v, 0, 0x4341);
+            } else {
+              const uint32_t* p = wp + 64 * g;
+              const uint32_t w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2);
+              const uint32_t v0 = __funnelshift_r(w0, w1, sh), v1 = __funnelshift_r(w1, w2, sh);
+              acc[q][g][0] += v0 & 0xFFFFu;
+              acc[q][g][1] += v0 >> 16;
+              acc[q][g][2] += v1 & 0xFFFFu;
+              acc[q][g][3] += v1 >> 16;
+            }
+          }
+        }
+      }
+    }
+    if (sizeof(T) == 1) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          acc[q][g][0] += ev[q][g] & 0xFFFFu;
+          acc[q][g][2] += ev[q][g] >> 16;
+          acc[q][g][1] += od[q][g] & 0xFFFFu;
+          acc[q][g][3] += od[q][g] >> 16;
+        }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (q < ntr) {
+      int32_t* yr = y + (int64_t)(tbase + q) * y_stride;
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t j = j0 + 128 * g + 4 * lane + e;
+          if (j < nout) yr[j] = (int32_t)acc[q][g][e];
+        }
+    }
+  }
+}
+
+cudaError_t launch_dedisp_direct(const DedispRange& r, int32_t cpad, cudaStream_t st) {
+  if (r.nout <= 0 || r.n_trials <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((r.n_trials + kDirectTrials - 1) / kDirectTrials),
+            (unsigned)((r.nout + kDirectTile - 1) / kDirectTile));
+  if (r.is_u16)
+    k_dedisp_direct<uint16_t><<<grid, 256, 0, st>>>(static_cast<const uint16_t*>(r.xd),
+                                                    r.xd_stride, cpad, r.m0, r.nout, r.n_trials,
+                                                    r.shifts, r.y, r.y_stride);
+  else
+    k_dedisp_direct<uint8_t><<<grid, 256, 0, st>>>(static_cast<const uint8_t*>(r.xd), r.xd_stride,
+                                                   cpad, r.m0, r.nout, r.n_trials, r.shifts, r.y,
+                                                   r.y_stride);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ moments
 
 struct U128 {

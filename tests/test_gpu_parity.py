@@ -167,18 +167,24 @@ def _tiled_regime(nchans=1001, nsamp=1 << 15):
 def test_kernel_choice():
     """Ranges whose delay classes fit the tiled kernel's tables run on it (512-sample tiles);
     x128 decimation (four channels of 255 x 128 do not fit a 16-bit lane) and the tiny
-    workload's 64 coarse channels (up to 63 classes per group) run on the per-output kernel."""
+    workload's 64 coarse channels (up to 63 classes per group) run on the direct kernel, and
+    DD_FLAG_NAIVE selects the one-thread-per-output kernel."""
     w = _tiled_regime()
     plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1)
     try:
         got = [plan.kernel(r) for r in range(len(w.ranges))]
     finally:
         plan.close()
-    assert got == [(1, 512)] * 7 + [(0, 0)]
+    assert got == [(dd.DD_KERNEL_TILED, 512)] * 7 + [(dd.DD_KERNEL_DIRECT, 0)]
     t = configs.tiny()
     plan = dd.Plan(t.freqs(), t.tsamp, t.ranges_array(), 4096, n_streams=1)
     try:
-        assert plan.kernel(0) == (0, 0)
+        assert plan.kernel(0) == (dd.DD_KERNEL_DIRECT, 0)
+    finally:
+        plan.close()
+    plan = dd.Plan(t.freqs(), t.tsamp, t.ranges_array(), 4096, n_streams=1, flags=dd.DD_FLAG_NAIVE)
+    try:
+        assert plan.kernel(0) == (dd.DD_KERNEL_PER_OUTPUT, 0)
     finally:
         plan.close()
 
