@@ -76,7 +76,7 @@ int wait_event(cudaEvent_t ev, int64_t timeout_ms) {
 // part is done.
 class StagingPool {
  public:
-  explicit StagingPool(int n) {
+  explicit StagingPool(int n) : n_(n) {
     for (int i = 0; i < n; ++i) threads_.emplace_back([this, i] { run(i); });
   }
   ~StagingPool() {
@@ -92,7 +92,7 @@ class StagingPool {
     dst_ = dst;
     src_ = src;
     bytes_ = bytes;
-    pending_ = (int)threads_.size();
+    pending_ = n_;
     ++gen_;
     cv_.notify_all();
     done_cv_.wait(l, [this] { return pending_ == 0; });
@@ -114,7 +114,7 @@ class StagingPool {
         src = src_;
         bytes = bytes_;
       }
-      const size_t n = threads_.size();
+      const size_t n = (size_t)n_;  // workers never touch threads_ (filled while they start)
       const size_t part = (bytes + n - 1) / n;
       const size_t b0 = std::min(bytes, part * (size_t)i), b1 = std::min(bytes, b0 + part);
       if (b1 > b0) std::memcpy(dst + b0, src + b0, b1 - b0);
@@ -124,6 +124,7 @@ class StagingPool {
       }
     }
   }
+  const int n_;
   std::vector<std::thread> threads_;
   std::mutex mu_;
   std::condition_variable cv_, done_cv_;
@@ -156,8 +157,9 @@ struct Slot {
 
 }  // namespace
 
-// How one range is dedispersed: the tiled DP4A kernel (with its tile shape and shared-memory
-// sizes) or, when the plan does not fit it, the one-thread-per-output kernel.
+// How one range is dedispersed: the tiled delay-class kernel (with its tile shape, staging
+// buffers and shared-memory sizes) or, when the plan does not fit it, the direct kernel (the
+// one-thread-per-output kernel with DD_FLAG_NAIVE).
 struct RangeKernel {
   bool tiled = false;
   int tt = 0;
@@ -194,10 +196,10 @@ struct dd_plan_s {
   dd_cand_t* h_cands = nullptr;    // pinned [max_cands]
   int64_t next_seq = 0, T_total = 0;
   int64_t launches = 0;
+  StagingPool* pool = nullptr;     // staging_threads > 0
   // dedispersion timing (DD_FLAG_TIMING): every launch is bracketed by an event pair; the pairs
   // are turned into [start, end) intervals against a common reference event and merged, so that
   // launches of different chunks running at the same time on different streams count once
-  StagingPool* pool = nullptr;     // staging_threads > 0
   std::vector<cudaEvent_t> tev;
   int64_t tev_used = 0;
   cudaEvent_t tref = nullptr;
