@@ -211,6 +211,30 @@ def test_search_peak_blocks_and_odd_widths(block):
     assert check(w, x, [4096] * 4, 2, block=block) > 0
 
 
+def test_search_widest_boxcars():
+    """Boxcars up to the largest width the plan accepts (1024 original samples: a 1024-sample
+    history in every search pass), in chunks of 4096 samples."""
+    w = _tiled_regime(nsamp=1 << 14)
+    w.widths = (1, 5, 64, 1000, 1024)
+    x = w.generate(_arrivals(w))
+    assert check(w, x, [4096] * 4, 2) > 0
+
+
+def test_single_trial_and_ragged_tiles():
+    """Ranges of 1 trial, 65 trials (a full 64-trial tile and a 1-trial tile) and 1 decimated
+    trial, through the tiled kernel, with a ragged last chunk."""
+    w = _tiled_regime(nsamp=1 << 14)
+    w.ranges = (configs.DMRange(0.0, 0.0625, 1, 1), configs.DMRange(1.0, 0.0625, 65, 1),
+                configs.DMRange(10.0, 0.125, 1, 2))
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1)
+    try:
+        assert [plan.kernel(r)[0] for r in range(3)] == [dd.DD_KERNEL_TILED] * 3
+    finally:
+        plan.close()
+    x = w.generate(_arrivals(w))
+    check(w, x, [4096] * 3 + [2048], 2)
+
+
 def test_one_thread_per_output_kernel_matches():
     """The testing-aid kernel (DD_FLAG_NAIVE) obeys the same contract as the tiled one."""
     w = _small_multirange(nsamp=1 << 14)
