@@ -443,7 +443,7 @@ def ooc_workload(args):
     decimation (6050 trials, overlap ~138k samples), 2^19-sample chunks over 4 streams, input in
     pageable host memory. One step = --ooc-chunks chunks of one continuing stream (a pool of two
     distinct seeded chunks, reused). Three ways in: pageable through the pinned staging threads
-    (Sec. 2.1; the headline), pageable through the driver, and pinned host memory."""
+    (Sec. 2.1; the headline), pageable through the CUDA driver, and pinned host memory."""
     import torch
 
     import paper_2101_00941_gb300 as dd

@@ -74,7 +74,7 @@ typedef struct {
   int32_t staging_threads; /* > 0: chunks in pageable host memory are first copied into a small
                               pinned buffer per stream by this many host threads, then sent
                               asynchronously (Sec. 2.1: pinned staging buffers filled by CPU
-                              threads); 0: pageable chunks are copied by the driver directly */
+                              threads); 0: the CUDA driver copies pageable chunks itself */
 } dd_opts_t;
 
 /* One single-pulse candidate (Sec. 2.2). */

@@ -36,7 +36,7 @@ def _as_input(part, kind):
         return torch.from_numpy(part).cuda()
     if kind == "pinned":
         return torch.from_numpy(part).pin_memory()
-    return np.ascontiguousarray(part)  # pageable (copied by the driver or by staging threads)
+    return np.ascontiguousarray(part)  # pageable (copied by the CUDA driver or staging threads)
 
 
 def run_gpu(w, x, chunk_sizes, n_streams, kind="device", flags=0, want_series=True,
