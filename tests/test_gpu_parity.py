@@ -235,6 +235,23 @@ def test_single_trial_and_ragged_tiles():
     check(w, x, [4096] * 3 + [2048], 2)
 
 
+def test_direct_kernel_huge_delay_spans():
+    """16 channels from 1500 down to 100 MHz at 1 ms: adjacent channels' delays differ by
+    thousands of samples (overlap 49151 samples), so the range runs on the direct kernel."""
+    w = configs.tiny()
+    w.nchans, w.fch1, w.foff, w.tsamp = 16, 1500.0, -1400.0 / 15, 1e-3
+    w.nsamp, w.widths = 1 << 17, (1, 2, 4, 8)
+    w.ranges = (configs.DMRange(100.0, 1.0, 20, 1),)
+    w.pulses = (configs.PulseSpec(110.0, 70000, 4, 40.0),)
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 1 << 16, n_streams=1)
+    try:
+        assert plan.kernel(0) == (dd.DD_KERNEL_DIRECT, 0)
+    finally:
+        plan.close()
+    x = w.generate(_arrivals(w))
+    check(w, x, [1 << 16, 1 << 16], 1)
+
+
 def test_one_thread_per_output_kernel_matches():
     """The testing-aid kernel (DD_FLAG_NAIVE) obeys the same contract as the tiled one."""
     w = _small_multirange(nsamp=1 << 14)
