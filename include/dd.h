@@ -339,6 +339,23 @@ int dd_serve_pending(dd_server_t server, int64_t* queued, int32_t* inflight);
 void dd_serve_destroy(dd_server_t server);
 
 /*
+ * dd_tiled_plan_check -- host-only check of the tiled kernel's plan for one range (no GPU, no
+ * CUDA call). Builds the plan-time tables the tiled kernel would use from a delay table and
+ * verifies them against it: each trial's pattern-word sequence adds, in every channel, the
+ * sample at that trial's own delay; class word ranges are aligned; every read stays inside the
+ * staged rows; the build work lists cover every block of every class once.
+ *   shifts       : int32 [n_trials][cpad], delays of one range in decimated samples, channels
+ *                  padded to cpad (a multiple of 8) by repeating the last channel
+ *   tile_samples : 512 or 256 (outputs per time tile)
+ *   ok           : receives 1 if the tiled kernel can run the range, else 0
+ *   violations   : receives the number of violated checks (0 expected; 0 when ok is 0)
+ * Errors: DD_ERR_ARG.
+ */
+int dd_tiled_plan_check(const int32_t* shifts, int32_t n_trials, int32_t cpad,
+                        int32_t decimation, int32_t tile_samples, int32_t* ok,
+                        int64_t* violations);
+
+/*
  * dd_selftest_wait -- failure-detection self-test of the device-side bounded wait. The tiled
  * dedispersion kernel waits on each stage's copy barrier for at most 2 s (or 2^26 polls); when
  * that runs out it sets an error bit that dd_candidates reports as DD_ERR_TIMEOUT, waits (again

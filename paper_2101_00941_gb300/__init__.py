@@ -29,7 +29,8 @@ DD_FLAG_DEVICE_INPUT = 4
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
 
-EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_selftest_wait", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
+EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_selftest_wait",
+           "dd_tiled_plan_check", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
            "dd_stats", "dd_sps_static", "dd_serve_create", "dd_serve_add_beam", "dd_serve_submit",
            "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_batch_create",
            "dd_batch_run", "dd_batch_wait", "dd_batch_info", "dd_batch_candidates",
@@ -86,6 +87,7 @@ def lib() -> ctypes.CDLL:
         L.dd_plan_info.argtypes = [vp, P(i64), P(i32), P(vp)]
         L.dd_plan_kernel.argtypes = [vp, i32, P(i32), P(i32)]
         L.dd_selftest_wait.argtypes = [i32, P(i32), P(ctypes.c_double)]
+        L.dd_tiled_plan_check.argtypes = [vp, i32, i32, i32, i32, P(i32), P(i64)]
         L.dd_run.argtypes = [vp, vp, i64, vp]
         L.dd_series.argtypes = [vp, i32, P(vp), P(i64), P(i64), P(i64)]
         L.sps_run.argtypes = [vp, vp, i32, f32]
@@ -180,6 +182,16 @@ def dd_selftest_wait(device: int = 0):
     t, ms = ctypes.c_int32(), ctypes.c_double()
     _check(lib().dd_selftest_wait(int(device), ctypes.byref(t), ctypes.byref(ms)))
     return t.value, ms.value
+
+
+def dd_tiled_plan_check(shifts, decimation: int, tile_samples: int = 512):
+    """Host-only check of the tiled plan of one range (see dd.h): (ok, violations).
+    `shifts` is int32 [n_trials][cpad] with cpad a multiple of 8."""
+    a = np.ascontiguousarray(shifts, dtype=np.int32)
+    ok, bad = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().dd_tiled_plan_check(a.ctypes.data, a.shape[0], a.shape[1], int(decimation),
+                                     int(tile_samples), ctypes.byref(ok), ctypes.byref(bad)))
+    return ok.value, bad.value
 
 
 def dd_run(plan: int, chunk, nsamp: int, cuda_stream: int = 0):

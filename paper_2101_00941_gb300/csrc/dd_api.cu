@@ -992,6 +992,18 @@ int dd_candidates(dd_plan_t p, int64_t seq, dd_cand_t* out, int64_t cap, int64_t
   return DD_OK;
 }
 
+int dd_tiled_plan_check(const int32_t* shifts, int32_t n_trials, int32_t cpad,
+                        int32_t decimation, int32_t tile_samples, int32_t* ok,
+                        int64_t* violations) {
+  if (!shifts || !ok || !violations) return fail(DD_ERR_ARG, "NULL argument");
+  if (n_trials < 1 || cpad < 8 || cpad % 8 || (tile_samples != 256 && tile_samples != 512))
+    return fail(DD_ERR_ARG, "need n_trials >= 1, cpad a multiple of 8, tile_samples 256 or 512");
+  int k = 0;
+  *violations = ddk::tiled_plan_check(shifts, n_trials, cpad, decimation, tile_samples, &k);
+  *ok = k;
+  return DD_OK;
+}
+
 int dd_selftest_wait(int32_t device, int32_t* timed_out, double* waited_ms) {
   if (!timed_out) return fail(DD_ERR_ARG, "timed_out is NULL");
   *timed_out = 0;

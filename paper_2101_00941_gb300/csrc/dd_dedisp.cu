@@ -718,6 +718,85 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
   X(uint8_t, 0, 512, 4) X(uint8_t, 0, 512, 3) X(uint8_t, 0, 256, 4) X(uint8_t, 0, 256, 3) \
   X(uint16_t, 1, 512, 4) X(uint16_t, 1, 512, 3) X(uint16_t, 1, 256, 4) X(uint16_t, 1, 256, 3)
 
+// Host: plan one range and verify the tables against the delay table they were built from,
+// independently of how they were built. Returns the number of violations of:
+//   - every trial's word sequence lies inside its class's words, and word u of the class adds,
+//     in every channel of the group, the sample at the trial's own delay (rel + offset);
+//   - class word ranges start and end on 16-byte boundaries;
+//   - the stage's copy start is the smallest first-trial delay of its rows, and every read of
+//     every trial stays inside the staged row;
+//   - the build work lists cover every 32-unit block of every class exactly once.
+int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, int tt,
+                         int* ok) {
+  const TiledPlan P = tiled_plan(tab, ntr, cpad, decimation, tt);
+  *ok = P.ok ? 1 : 0;
+  if (!P.ok) return 0;
+  const bool u16 = decimation > 1;
+  const int U = u16 ? 2 : 4, SEG = kSegBytes / (u16 ? 2 : 1);
+  const int ngroups = cpad / kG, nstages = (ngroups + kNG - 1) / kNG;
+  const int ntiles = (ntr + kTileTrials - 1) / kTileTrials;
+  const StageTab* tabs = reinterpret_cast<const StageTab*>(P.tabs.data());
+  int64_t bad = 0;
+  for (int ti = 0; ti < ntiles; ++ti) {
+    const int t0 = ti * kTileTrials, n = std::min(kTileTrials, ntr - t0);
+    for (int s = 0; s < nstages; ++s) {
+      const StageTab& st = tabs[(size_t)ti * nstages + s];
+      int32_t xmin = INT32_MAX;
+      for (int c = s * kRows; c < std::min(cpad, (s + 1) * kRows); ++c)
+        xmin = std::min(xmin, tab[(int64_t)t0 * cpad + c]);
+      bad += st.xmin != xmin;
+      for (int t = t0; t < t0 + n; ++t)
+        for (int c = s * kRows; c < std::min(cpad, (s + 1) * kRows); ++c)
+          bad += (int64_t)tab[(int64_t)t * cpad + c] - xmin + tt + 32 + SEG - 1 > P.row_slot;
+      std::vector<int> covered;  // blocks of every (group, class), in order
+      std::vector<int> first_block(kNG * kMaxCls + 1, 0);
+      for (int gl = 0; gl < kNG; ++gl)
+        for (int p = 0; p < kMaxCls; ++p) {
+          const int nb = p < st.g[gl].ncls ? (st.g[gl].cls[p].zlen / U + 31) / 32 : 0;
+          first_block[gl * kMaxCls + p + 1] = first_block[gl * kMaxCls + p] + nb;
+        }
+      covered.assign(first_block.back(), 0);
+      for (int w = 0; w < kWarps; ++w)
+        for (int k = 0; k < st.nwork[w]; ++k) {
+          const uint32_t wk = st.work[w][k];
+          const int gl = (int)((wk >> 4) & 1), p = (int)(wk & 15);
+          const int b0 = (int)((wk >> 8) & 255), nb = (int)(wk >> 16);
+          for (int b = b0; b < b0 + nb; ++b) {
+            const int idx = first_block[gl * kMaxCls + p] + b;
+            if (p >= st.g[gl].ncls || idx >= first_block[gl * kMaxCls + p + 1]) {
+              ++bad;
+            } else {
+              ++covered[idx];
+            }
+          }
+        }
+      for (int v : covered) bad += v != 1;
+      for (int gl = 0; gl < kNG && s * kNG + gl < ngroups; ++gl) {
+        const GroupTab& gt = st.g[gl];
+        const int c0 = (s * kNG + gl) * kG;
+        for (int p = 0; p < gt.ncls; ++p) bad += (gt.cls[p].zoff % 4) + (gt.cls[p].zlen % 4) != 0;
+        for (int i = 0; i < n; ++i) {
+          const int z = gt.zstart[i];
+          int p = 0;
+          while (p < gt.ncls &&
+                 !(gt.cls[p].zoff <= z && z + tt <= gt.cls[p].zoff + gt.cls[p].zlen))
+            ++p;
+          if (p == gt.ncls) {
+            ++bad;
+            continue;
+          }
+          for (int q = 0; q < kG; ++q) {
+            const int64_t want = (int64_t)tab[(int64_t)(t0 + i) * cpad + c0 + q] -
+                                 tab[(int64_t)t0 * cpad + c0 + q];
+            bad += (int64_t)gt.cls[p].rel[q] + (z - gt.cls[p].zoff) != want;
+          }
+        }
+      }
+    }
+  }
+  return bad;
+}
+
 cudaError_t prepare_tiled(int is_u16, int tt, int nstage, size_t smem) {
 #define DD_PREPARE(T, U16, TT, NS) \
   if (is_u16 == U16 && tt == TT && nstage == NS) return prepare_t<T, TT, NS>(smem);

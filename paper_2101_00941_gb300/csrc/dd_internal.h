@@ -96,6 +96,8 @@ struct TiledPlan {
 
 int tiled_tile_samples(int is_u16, int choice);
 TiledPlan tiled_plan(const int32_t* shifts, int ntr, int cpad, int decimation, int tt);
+int64_t tiled_plan_check(const int32_t* shifts, int ntr, int cpad, int decimation, int tt,
+                         int* ok);
 cudaError_t prepare_tiled(int is_u16, int tt, int nstage, size_t smem);
 // One CTA waits, with the tiled kernel's bound, on a barrier nothing completes; sets *err bit 0
 // when the bound runs out.
