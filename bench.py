@@ -616,6 +616,8 @@ def main(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": w.nsamp * w.nchans,
                 "d2h_bytes_per_step": int(ncand_e2e / args.steps * 32 + nchunks * 8),
                 "real_time_factor": obs / (ms_e2e * 1e-3 / args.steps),
+                # host-to-device time the streams did not hide: e2e step minus resident step
+                "exposed_copy_ms_per_chunk": max(0.0, (ms_e2e - ms) / args.steps / nchunks),
                 "chunk_latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                                      "p99": 1e3 * float(np.percentile(lat, 99))}},
         "gpu_launches": launches,
