@@ -252,6 +252,20 @@ def test_direct_kernel_huge_delay_spans():
     check(w, x, [1 << 16, 1 << 16], 1)
 
 
+def test_tiled_kernel_odd_group_count():
+    """993 channels (padded to 1000: 125 eight-channel groups, so the last stage holds one
+    group), every trial of two ranges, in ragged chunks."""
+    w = _tiled_regime(nchans=993, nsamp=1 << 14)
+    w.ranges = (configs.DMRange(0.0, 0.0625, 100, 1), configs.DMRange(6.25, 0.125, 50, 2))
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1)
+    try:
+        assert [plan.kernel(r)[0] for r in range(2)] == [dd.DD_KERNEL_TILED] * 2
+    finally:
+        plan.close()
+    x = w.generate(_arrivals(w))
+    assert check(w, x, [4096] * 3 + [2048], 2) >= 0
+
+
 def test_one_thread_per_output_kernel_matches():
     """The testing-aid kernel (DD_FLAG_NAIVE) obeys the same contract as the tiled one."""
     w = _small_multirange(nsamp=1 << 14)

@@ -58,6 +58,16 @@ def test_ragged_channels_and_trial_tiles():
         assert ok == (1 if r.decimation <= 64 else 0), r
 
 
+def test_odd_group_count():
+    """993 channels: padded to 1000, 125 eight-channel groups, so the last stage holds one."""
+    ranges = (configs.DMRange(0.0, 0.0625, 100, 1), configs.DMRange(6.25, 0.125, 50, 2))
+    w = configs.mid(nsamp=1 << 15, nchans=4096, ranges=ranges)
+    w.nchans, w.foff = 993, -300.0 / 1024
+    for tab, r in zip(_tables(w), w.ranges):
+        assert tab.shape[1] == 1000
+        assert dd.dd_tiled_plan_check(tab, r.decimation, 512) == (1, 0), r
+
+
 def test_coarse_channels_and_bad_tables_are_refused():
     w = configs.tiny()  # 64 coarse channels: up to 63 delay classes per group
     (tab,) = _tables(w)
