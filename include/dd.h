@@ -50,6 +50,8 @@ extern "C" {
 #define DD_FLAG_NAIVE 2u    /* use the one-thread-per-output dedispersion kernel (testing aid) */
 #define DD_FLAG_DEVICE_INPUT 4u /* chunks are always in device memory: no staging buffer is
                                    allocated and host chunks are refused (DD_ERR_ARG) */
+#define DD_FLAG_TILE256 8u  /* plan the tiled kernel with 256-sample time tiles first (testing
+                               aid; 512-sample tiles are tried first otherwise) */
 
 typedef struct dd_plan_s* dd_plan_t;
 

@@ -26,6 +26,7 @@ DD_ERR_STATE = -6
 DD_FLAG_TIMING = 1
 DD_FLAG_NAIVE = 2
 DD_FLAG_DEVICE_INPUT = 4
+DD_FLAG_TILE256 = 8
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
 

@@ -641,7 +641,8 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     if (!(o.flags & DD_FLAG_NAIVE)) {
       for (int r = 0; r < nranges; ++r) {
         const bool u16 = ranges[r].decimation > 1;
-        for (int choice = 0; choice < 2; ++choice) {
+        const int first = (o.flags & DD_FLAG_TILE256) ? 1 : 0;
+        for (int choice = first; choice < 2; ++choice) {
           const int tt = ddk::tiled_tile_samples(u16, choice);
           ddk::TiledPlan tp = ddk::tiled_plan(&full[(size_t)p->row0[r] * p->Cp],
                                               ranges[r].n_trials, p->Cp,

@@ -266,6 +266,21 @@ def test_tiled_kernel_odd_group_count():
     assert check(w, x, [4096] * 3 + [2048], 2) >= 0
 
 
+def test_tiled_kernel_256_sample_tiles():
+    """The 256-sample-tile instances (uint8 and uint16), forced by DD_FLAG_TILE256, on every
+    trial of ranges x1 .. x8, in ragged chunks."""
+    w = _tiled_regime(nsamp=1 << 14)
+    w.ranges = w.ranges[:4]
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1,
+                   flags=dd.DD_FLAG_TILE256)
+    try:
+        assert [plan.kernel(r) for r in range(4)] == [(dd.DD_KERNEL_TILED, 256)] * 4
+    finally:
+        plan.close()
+    x = w.generate(_arrivals(w))
+    assert check(w, x, [4096] * 3 + [2048], 2, flags=dd.DD_FLAG_TILE256) >= 0
+
+
 def test_one_thread_per_output_kernel_matches():
     """The testing-aid kernel (DD_FLAG_NAIVE) obeys the same contract as the tiled one."""
     w = _small_multirange(nsamp=1 << 14)
