@@ -66,7 +66,7 @@ typedef struct {
 
 typedef struct {
   int64_t chunk_len;   /* most new samples one dd_run call may deliver (Sec. 1: a time chunk);
-                          a multiple of 256 */
+                          a multiple of 256, at most 65535 * 256 = 16776960 */
   int32_t n_streams;   /* CUDA streams the chunks rotate over (Sec. 2: stream IDs), 1..16 */
   int32_t max_width;   /* largest boxcar width (original samples) sps_run will be given */
   int32_t peak_block;  /* samples per candidate block (decimated samples of each range), >= 1 */

@@ -529,8 +529,9 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
   }
   if (total_rows > (1 << 24)) return fail(DD_ERR_ARG, "too many trials");
   const dd_opts_t& o = *opts;
-  if (o.chunk_len < 256 || o.chunk_len % 256 != 0 || o.chunk_len > (int64_t(1) << 31))
-    return fail(DD_ERR_ARG, "chunk_len %lld must be a positive multiple of 256",
+  // launch grids: time tiles of >= 256 outputs and one row per trial in a 65535-wide dimension
+  if (o.chunk_len < 256 || o.chunk_len % 256 != 0 || o.chunk_len > int64_t(65535) * 256)
+    return fail(DD_ERR_ARG, "chunk_len %lld must be a multiple of 256 in 256..16776960",
                 (long long)o.chunk_len);
   if (o.n_streams < 1 || o.n_streams > 16)
     return fail(DD_ERR_ARG, "n_streams %d outside 1..16", o.n_streams);

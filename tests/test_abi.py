@@ -65,6 +65,7 @@ def _plan(lib, nchans=16, freqs=None, ranges=((0.0, 1.0, 8, 1),), **kw):
     dict(ranges=((0.0, 1.0, 8, 3),)), dict(ranges=((0.0, 1.0, 0, 1),)),
     dict(ranges=((-1.0, 1.0, 8, 1),)), dict(freqs=[1500.0, -1.0] + [1400.0] * 14),
     dict(nchans=8192, max_width=1024), dict(staging_threads=-1), dict(staging_threads=65),
+    dict(chunk_len=1 << 24), dict(ranges=((0.0, 1.0, 65536, 1),)),
 ])
 def test_invalid_plans_are_rejected_before_any_gpu_work(lib, kw):
     assert _plan(lib, **kw) == dd.DD_ERR_ARG
