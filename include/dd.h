@@ -179,9 +179,11 @@ int sps_run(dd_plan_t plan, const int32_t* widths, int32_t nwidths, float thresh
  *   out    : caller-owned host array of cap entries, sorted by (range, trial, t_start, width)
  *   ncands : receives the number of candidates found
  *   timeout_ms : bound on the wait (<= 0: 600000)
- * Errors: DD_ERR_STATE (unknown, recycled or unsearched chunk), DD_ERR_TIMEOUT, DD_ERR_CAP
- * (more than cap or than opts.max_cands; *ncands holds the true count, out holds the first cap
- * found in sorted order of those kept), DD_ERR_CUDA.
+ * Errors: DD_ERR_STATE (unknown, recycled or unsearched chunk), DD_ERR_TIMEOUT (the wait ran
+ * out, or a dedispersion kernel of this chunk ran out of its bounded device-side wait, so the
+ * chunk's results are not valid; later chunks are not affected), DD_ERR_CAP (more than cap or
+ * than opts.max_cands; *ncands holds the true count, out holds the first cap found in sorted
+ * order of those kept), DD_ERR_CUDA.
  */
 int dd_candidates(dd_plan_t plan, int64_t seq, dd_cand_t* out, int64_t cap, int64_t* ncands,
                   int64_t timeout_ms);
@@ -316,7 +318,11 @@ int dd_batch_create(int32_t nbeams, const dd_batch_beam_t* beams, const dd_range
                     int32_t nwidths, float threshold, int64_t cap_per_chunk, uint32_t flags,
                     dd_batch_t* out);
 
-/* dd_batch_run -- enqueue one step (asynchronous); dd_batch_wait waits for it (bounded). */
+/* dd_batch_run -- enqueue one step (asynchronous); dd_batch_wait waits for it (bounded).
+ * dd_batch_wait errors: DD_ERR_TIMEOUT when the step does not finish within timeout_ms (<= 0:
+ * 600000), and also when a dedispersion kernel of the step ran out of its bounded device-side
+ * wait (the step's candidates are then not valid and dd_batch_candidates refuses them until a
+ * later step succeeds), DD_ERR_CUDA. */
 int dd_batch_run(dd_batch_t batch);
 int dd_batch_wait(dd_batch_t batch, int64_t timeout_ms);
 

@@ -197,6 +197,7 @@ struct dd_plan_s {
   int64_t next_seq = 0, T_total = 0;
   int64_t launches = 0;
   StagingPool* pool = nullptr;     // staging_threads > 0
+  int32_t* err_word = nullptr;     // if set, kernel error bits go here instead of the slot's
   // dedispersion timing (DD_FLAG_TIMING): every launch is bracketed by an event pair; the pairs
   // are turned into [start, end) intervals against a common reference event and merged, so that
   // launches of different chunks running at the same time on different streams count once
@@ -483,6 +484,8 @@ int plan_autotune(dd_plan_s* p) {
 }
 
 int range_tile(dd_plan_s* p, int r) { return p->rk[r].tiled ? p->rk[r].tt : 0; }
+
+void plan_redirect_errors(dd_plan_s* p, int32_t* err) { p->err_word = err; }
 
 int chunk_state(dd_plan_s* p, int64_t seq) {
   const int64_t S = (int64_t)p->slots.size();
@@ -803,6 +806,8 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
     DD_CK(cudaMemcpyAsync(s.staging, chunk, (size_t)nsamp * p->C, cudaMemcpyHostToDevice, st));
     src = s.staging;
   }
+  // the slot's kernel error bits describe this chunk only
+  if (!p->err_word) DD_CK(cudaMemsetAsync(s.d_count + 1, 0, sizeof(unsigned long long), st));
   const int64_t H = p->H;
   if (seq > 0 && H > 0)
     DD_CK(cudaMemcpy2DAsync(s.ring1, p->R1, p->hist, H, H, p->Cp, cudaMemcpyDeviceToDevice, st));
@@ -861,7 +866,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       A.zcap = K.zcap;
       A.nstage = K.nstage;
       A.tabs = K.d_tabs;
-      A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
+      A.err = p->err_word ? p->err_word : reinterpret_cast<int32_t*>(s.d_count + 1);
       DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, st));
       p->launches += 1;
     } else if (p->opts.flags & DD_FLAG_NAIVE) {

@@ -26,8 +26,10 @@ struct dd_batch_s {
   float threshold = 0;
   int64_t total_chunks = 0;
   dd_cand_t* d_cands = nullptr;             // [total_chunks][cap]
-  unsigned long long* d_counts = nullptr;   // [total_chunks]
-  unsigned long long* h_counts = nullptr;   // pinned [total_chunks]
+  // [total_chunks] candidate counts, then one word of dedispersion-kernel error bits (every
+  // plan's tiled kernels report into it; cleared at the start of each step)
+  unsigned long long* d_counts = nullptr;   // [total_chunks + 1]
+  unsigned long long* h_counts = nullptr;   // pinned [total_chunks + 1]
   dd_cand_t* h_cands = nullptr;             // pinned [cap]
   cudaStream_t root = nullptr;
   std::vector<cudaStream_t> streams;        // every plan's streams
@@ -67,7 +69,10 @@ int ck(cudaError_t e, const char* what) {
 
 // Enqueue one whole step on the beams' own streams, forked from and joined back to `root`.
 int enqueue_step(dd_batch_s* b) {
-  int rc = ck(cudaEventRecord(b->fork, b->root), "fork");
+  int rc = ck(cudaMemsetAsync(b->d_counts + b->total_chunks, 0, sizeof(unsigned long long),
+                              b->root),
+              "error word");
+  if (rc == DD_OK) rc = ck(cudaEventRecord(b->fork, b->root), "fork");
   for (size_t k = 0; rc == DD_OK && k < b->streams.size(); ++k)
     rc = ck(cudaStreamWaitEvent(b->streams[k], b->fork, 0), "fork wait");
   const int64_t L = b->chunk_len;
@@ -91,7 +96,8 @@ int enqueue_step(dd_batch_s* b) {
     if (rc == DD_OK) rc = ck(cudaStreamWaitEvent(b->root, b->join[k], 0), "join wait");
   }
   if (rc == DD_OK)
-    rc = ck(cudaMemcpyAsync(b->h_counts, b->d_counts, sizeof(unsigned long long) * b->total_chunks,
+    rc = ck(cudaMemcpyAsync(b->h_counts, b->d_counts,
+                            sizeof(unsigned long long) * (b->total_chunks + 1),
                             cudaMemcpyDeviceToHost, b->root),
             "count readback");
   return rc;
@@ -166,16 +172,21 @@ int dd_batch_create(int32_t nbeams, const dd_batch_beam_t* beams, const dd_range
     rc = ddk::report_error(DD_ERR_NOMEM, "dd_batch_create: candidate buffers");
   }
   if (rc == DD_OK &&
-      cudaMalloc(&b->d_counts, sizeof(unsigned long long) * b->total_chunks) != cudaSuccess) {
+      cudaMalloc(&b->d_counts, sizeof(unsigned long long) * (b->total_chunks + 1)) !=
+          cudaSuccess) {
     cudaGetLastError();
     rc = ddk::report_error(DD_ERR_NOMEM, "dd_batch_create: counts");
   }
   if (rc == DD_OK &&
-      (cudaMallocHost(&b->h_counts, sizeof(unsigned long long) * b->total_chunks) != cudaSuccess ||
+      (cudaMallocHost(&b->h_counts, sizeof(unsigned long long) * (b->total_chunks + 1)) !=
+           cudaSuccess ||
        cudaMallocHost(&b->h_cands, sizeof(dd_cand_t) * b->cap) != cudaSuccess)) {
     cudaGetLastError();
     rc = ddk::report_error(DD_ERR_NOMEM, "dd_batch_create: pinned buffers");
   }
+  if (rc == DD_OK)
+    for (auto p : b->plans)
+      ddk::plan_redirect_errors(p, reinterpret_cast<int32_t*>(b->d_counts + b->total_chunks));
   if (rc == DD_OK && (flags & DD_BATCH_GRAPH)) {
     // capture one whole step; every plan starts at sample 0, so the graph replays correctly
     rc = reset_all(b);
@@ -225,6 +236,10 @@ int dd_batch_wait(dd_batch_t b, int64_t timeout_ms) {
       return ddk::report_error(DD_ERR_TIMEOUT, "dd_batch_wait: the step did not finish in time");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+  if (b->h_counts[b->total_chunks] != 0)
+    return ddk::report_error(DD_ERR_TIMEOUT,
+                             "dd_batch_wait: a dedispersion kernel stopped early; the step's "
+                             "results are not valid");
   b->counts_ready = true;
   return DD_OK;
 }

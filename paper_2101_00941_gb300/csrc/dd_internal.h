@@ -120,7 +120,9 @@ int chunk_state(dd_plan_s* plan, int64_t seq);
 // Batch support: wait for the plan and start its stream again at sample 0; the plan's streams;
 // outputs (DM-trial*samples) of a stream of nsamp samples; the search of the latest chunk into
 // caller-chosen device buffers (count cleared first; no host readback); choose each tiled
-// range's time tile by timing the candidates; the chosen tile (0: simple kernel).
+// range's time tile by timing the candidates; the chosen tile (0: simple kernel); send the
+// dedispersion kernels' error bits to a caller-owned device word (the caller clears and reads
+// it) instead of the slot's own, which dd_run clears for each chunk.
 int plan_reset(dd_plan_s* plan);
 void plan_streams(dd_plan_s* plan, std::vector<cudaStream_t>* out);
 int64_t plan_outputs(dd_plan_s* plan, int64_t nsamp);
@@ -128,6 +130,7 @@ int sps_enqueue(dd_plan_s* plan, const int32_t* widths, int32_t nwidths, float t
                 dd_cand_t* cands, unsigned long long* count, int64_t cap);
 int plan_autotune(dd_plan_s* plan);
 int range_tile(dd_plan_s* plan, int r);
+void plan_redirect_errors(dd_plan_s* plan, int32_t* err);
 
 // ---- launchers (dd_kernels.cu); each returns the cudaGetLastError() of its launch
 cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t cpad, double fref,
