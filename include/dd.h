@@ -278,8 +278,10 @@ int dd_serve_add_beam(dd_server_t server, const double* freqs_mhz, int32_t nchan
 /* dd_serve_submit -- queue the next chunk of a beam (as dd_run: time-major uint8
  * [nsamp][nchans], host or device memory, caller-owned and unchanged until its result is
  * polled). The chunk's candidates are copied to out (host, cap entries, sorted as by
- * dd_candidates) before its result is reported. Returns without waiting (it may wait briefly
- * while the dispatcher holds the server's lock). Errors: DD_ERR_ARG. */
+ * dd_candidates) before its result is reported. Returns without waiting for the GPU (the
+ * dispatcher holds the server's lock only to move requests between queues, never across a copy,
+ * a launch or a sort); the submission time, from which queue_ms and latency_ms are measured, is
+ * taken on entry. Errors: DD_ERR_ARG. */
 int dd_serve_submit(dd_server_t server, int32_t beam, const uint8_t* chunk, int64_t nsamp,
                     dd_cand_t* out, int64_t cap, int64_t* ticket);
 

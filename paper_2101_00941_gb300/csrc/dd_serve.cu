@@ -55,6 +55,7 @@ struct dd_server_s {
   int64_t budget = 0, used = 0;
   std::vector<Beam*> beams;
   std::mutex mu;
+  std::mutex add_mu;  // one dd_serve_add_beam at a time: its memory measurement is a difference
   std::condition_variable work_cv, done_cv;
   std::deque<dd_serve_result_t> done;
   std::thread worker;
@@ -67,63 +68,78 @@ struct dd_server_s {
 
 void dd_server_s::run() {
   cudaSetDevice(device);
+  // Only this thread calls into the plans; the lock guards the queues, counters and the beam
+  // list, and is released around every plan call so that submitters and pollers never wait
+  // for a copy, a launch sequence or a candidate sort.
   std::unique_lock<std::mutex> lk(mu);
+  std::vector<std::pair<Beam*, Request>> ready;
+  std::vector<int> ready_state;
   while (!stop) {
     bool progress = false;
-    // completions: the oldest in-flight chunk of every beam
+    // completions: the oldest in-flight chunks of every beam whose search has finished
+    ready.clear();
+    ready_state.clear();
     for (int b = 0; b < (int)beams.size(); ++b) {
       Beam& bm = *beams[b];
       while (!bm.inflight.empty()) {
-        Request& r = bm.inflight.front();
-        const int st = ddk::chunk_state(bm.plan, r.seq);
+        const int st = ddk::chunk_state(bm.plan, bm.inflight.front().seq);
         if (st == 0) break;
-        dd_serve_result_t res;
-        res.ticket = r.ticket;
-        res.beam = b;
-        res.seq = r.seq;
-        int64_t n = 0;
-        res.status = st < 0 ? st : dd_candidates(bm.plan, r.seq, r.out, r.cap, &n, 0);
-        const auto now = Clock::now();
-        res.ncands = n;
-        res.queue_ms = ms_between(r.t_submit, r.t_admit);
-        res.latency_ms = ms_between(r.t_submit, now);
-        done.push_back(res);
+        ready.emplace_back(&bm, bm.inflight.front());
+        ready_state.push_back(st);
         bm.inflight.pop_front();
-        --inflight;
-        progress = true;
       }
     }
-    if (progress) done_cv.notify_all();
+    if (!ready.empty()) {
+      lk.unlock();
+      std::vector<dd_serve_result_t> res(ready.size());
+      for (size_t k = 0; k < ready.size(); ++k) {
+        const Request& r = ready[k].second;
+        int64_t n = 0;
+        const int st = ready_state[k];
+        res[k].ticket = r.ticket;
+        res[k].beam = r.beam;
+        res[k].seq = r.seq;
+        res[k].status = st < 0 ? st : dd_candidates(ready[k].first->plan, r.seq, r.out, r.cap,
+                                                    &n, 0);
+        const auto now = Clock::now();
+        res[k].ncands = n;
+        res[k].queue_ms = ms_between(r.t_submit, r.t_admit);
+        res[k].latency_ms = ms_between(r.t_submit, now);
+      }
+      lk.lock();
+      for (auto& x : res) done.push_back(x);
+      inflight -= (int)ready.size();
+      done_cv.notify_all();
+      progress = true;
+    }
     // admissions: earliest submitted request whose beam has a free slot
-    while (inflight < max_inflight) {
+    while (!stop && inflight < max_inflight) {
       Beam* pick = nullptr;
-      int pick_b = -1;
-      for (int b = 0; b < (int)beams.size(); ++b) {
-        Beam& bm = *beams[b];
-        if (bm.queue.empty() || (int)bm.inflight.size() >= bm.n_streams) continue;
-        if (!pick || bm.queue.front().ticket < pick->queue.front().ticket) {
-          pick = &bm;
-          pick_b = b;
-        }
+      for (auto* bm : beams) {
+        if (bm->queue.empty() || (int)bm->inflight.size() >= bm->n_streams) continue;
+        if (!pick || bm->queue.front().ticket < pick->queue.front().ticket) pick = bm;
       }
       if (!pick) break;
       Request r = pick->queue.front();
       pick->queue.pop_front();
       r.t_admit = Clock::now();
+      ++inflight;  // reserved while the chunk is being enqueued
+      lk.unlock();
       int rc = dd_run(pick->plan, r.chunk, r.nsamp, nullptr);
       if (rc == DD_OK) {
         r.seq = pick->next_seq++;
         rc = sps_run(pick->plan, pick->widths.data(), (int32_t)pick->widths.size(),
                      pick->threshold);
       }
+      lk.lock();
       if (rc != DD_OK) {
-        dd_serve_result_t res{r.ticket, pick_b, rc, -1, 0, 0.0, 0.0};
+        --inflight;
+        dd_serve_result_t res{r.ticket, r.beam, rc, -1, 0, 0.0, 0.0};
         done.push_back(res);
         done_cv.notify_all();
         continue;
       }
       pick->inflight.push_back(r);
-      ++inflight;
       progress = true;
     }
     if (!progress) work_cv.wait_for(lk, std::chrono::microseconds(inflight ? 50 : 2000));
@@ -161,6 +177,7 @@ int dd_serve_add_beam(dd_server_t s, const double* freqs_mhz, int32_t nchans, do
     return ddk::report_error(DD_ERR_CUDA, "dd_serve_add_beam: cudaSetDevice failed");
   dd_opts_t o = *opts;
   o.device = s->device;
+  std::lock_guard<std::mutex> add_lk(s->add_mu);
   size_t free0 = 0, free1 = 0, total = 0;
   cudaMemGetInfo(&free0, &total);
   dd_plan_t plan = nullptr;
@@ -190,6 +207,7 @@ int dd_serve_submit(dd_server_t s, int32_t beam, const uint8_t* chunk, int64_t n
                     dd_cand_t* out, int64_t cap, int64_t* ticket) {
   if (!s || !chunk || (!out && cap > 0) || cap < 0)
     return ddk::report_error(DD_ERR_ARG, "dd_serve_submit: bad argument");
+  const auto t_submit = Clock::now();  // before the lock: time spent waiting for it counts
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (beam < 0 || beam >= (int32_t)s->beams.size())
@@ -201,8 +219,8 @@ int dd_serve_submit(dd_server_t s, int32_t beam, const uint8_t* chunk, int64_t n
     r.nsamp = nsamp;
     r.out = out;
     r.cap = cap;
-    r.t_submit = Clock::now();
-    r.t_admit = r.t_submit;
+    r.t_submit = t_submit;
+    r.t_admit = t_submit;
     r.seq = -1;
     s->beams[beam]->queue.push_back(r);
     if (ticket) *ticket = r.ticket;
