@@ -81,3 +81,40 @@ def test_device_input_plans_refuse_host_chunks():
         assert e.value.code == dd.DD_ERR_ARG
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_of_tiled_beams(graph):
+    """Beams of 256 fine channels whose ranges (x1, x2) run on the tiled kernel, whose error
+    bits a batch collects in a word of its own: the step reports that word clean, and every
+    (beam, chunk) has exactly the candidates of the beam alone."""
+    dd.build()
+    ranges = (configs.DMRange(0.0, 0.0625, 70, 1), configs.DMRange(4.375, 0.125, 40, 2))
+    beams = []
+    for k, nsamp in enumerate((12288, 8192)):
+        w = configs.mid(nsamp=nsamp, chunk_len=4096, n_streams=1, npulses=3, nchans=4096,
+                        ranges=ranges, index=40 + k)
+        w.nchans, w.foff = 256, -300.0 / 1024
+        w.pulses = (configs.PulseSpec(2.5 + 3 * k, 3000, 8, 20 * 16.0 / (8 * 256) ** 0.5),
+                    configs.PulseSpec(6.0, nsamp - 2500, 16, 20 * 16.0 / (16 * 256) ** 0.5))
+        f = w.freqs()
+        x = w.generate(lambda dm, f=f, w=w: oracle.delay_samples(f, w.tsamp, dm))
+        beams.append((w, x))
+    want = [_alone(w, x) for w, x in beams]
+    w0 = beams[0][0]
+    dev = [torch.from_numpy(x).cuda() for _, x in beams]
+    b = dd.Batch([(w.freqs(), w.tsamp, d) for (w, _), d in zip(beams, dev)],
+                 w0.ranges_array(), 4096, w0.widths, w0.threshold, n_streams=2, graph=graph)
+    try:
+        for step in range(2):
+            b.run()
+            b.wait()
+            for i in range(len(beams)):
+                nchunks, _, tile = b.info(i)
+                assert tile > 0  # range 0 runs on the tiled kernel
+                assert nchunks == len(want[i])
+                for k in range(nchunks):
+                    np.testing.assert_array_equal(b.candidates(i, k), want[i][k])
+        assert sum(c.size for ws in want for c in ws) > 0
+    finally:
+        b.close()
