@@ -41,7 +41,7 @@ ALU_PEAK_ADDS = 152 * 128 * 2070e6
 # DRAM bytes (read + write) of the four dedispersion launches of one full 131072-sample chunk
 # window of the 4096-channel workload, from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_dedisp_tiled_mid_4096ch.md).
-DEDISP_DRAM_BYTES_PER_FULL_CHUNK = 1.313e9 + 0.800e9 + 0.391e9 + 0.201e9
+DEDISP_DRAM_BYTES_PER_FULL_CHUNK = 1.312e9 + 0.791e9 + 0.386e9 + 0.196e9
 
 
 def dist_info():

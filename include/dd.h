@@ -121,7 +121,7 @@ int dd_plan_info(dd_plan_t plan, int64_t* overlap, int32_t* ntrials, const int32
  * dd_plan_kernel -- which dedispersion kernel range `range` (0-based, plan order) runs on.
  *   kind         : DD_KERNEL_TILED (delay classes shared by a 64-trial tile), DD_KERNEL_DIRECT
  *                  (the fallback where the range's delay classes or decimation exceed the tiled
- *                  kernel's limits: coarse channels, decimation above x64) or
+ *                  kernel's limits: coarse channels, decimation above x16) or
  *                  DD_KERNEL_PER_OUTPUT (one thread per output, with DD_FLAG_NAIVE) (may be NULL)
  *   tile_samples : outputs per time tile of the tiled kernel, 0 for the others (may be NULL)
  * Errors: DD_ERR_ARG (NULL plan, range out of bounds).
@@ -351,9 +351,10 @@ void dd_serve_destroy(dd_server_t server);
 /*
  * dd_tiled_plan_check -- host-only check of the tiled kernel's plan for one range (no GPU, no
  * CUDA call). Builds the plan-time tables the tiled kernel would use from a delay table and
- * verifies them against it: each trial's pattern-word sequence adds, in every channel, the
- * sample at that trial's own delay; class word ranges are aligned; every read stays inside the
- * staged rows; the build work lists cover every block of every class once.
+ * verifies them against it: each trial's pair words lie in one plane (even or odd words) of its
+ * delay class and stand for class words that add, in every channel, the sample at that trial's
+ * own delay; class word ranges are aligned; every read stays inside the staged rows; the build
+ * work lists cover every block of every class once.
  *   shifts       : int32 [n_trials][cpad], delays of one range in decimated samples, channels
  *                  padded to cpad (a multiple of 8) by repeating the last channel
  *   tile_samples : 512 or 256 (outputs per time tile)

@@ -5,23 +5,27 @@
 // range and walks the channels in stages of kNG groups of eight channels.
 //
 //   * Delay classes. For an 8-channel group the tile's trials fall into a few classes by the
-//     relative delays (r0..r7) of the eight channels. A class shares one "pattern word" sequence
-//        Z_p[u] = (x[c0][a+u+r0] + .. + x[c3][a+u+r3]) | (x[c4][a+u+r4] + .. + x[c7][..]) << 16
-//     -- two 16-bit lanes, each the exact sum of four channels (4 x 255 x d < 2^16 for d <= 64)
-//     -- that each of its trials reads at its own base offset. The classes depend on the delay
-//     table only, so the plan computes them once (tiled_plan, below) as one fixed-size table per
-//     (trial tile, stage), together with a balanced split of the stage's word building over the
-//     warps; the kernel never searches for them.
+//     relative delays (r0..r7) of the eight channels. A class shares one sequence of sums
+//        S_p[u] = x[c0][a+u+r0] + .. + x[c7][a+u+r7]
+//     that each of its trials reads at its own base offset, stored as "pair words"
+//        Z_p[u] = S_p[u] | S_p[u+1] << 16
+//     (exact in 16-bit lanes: two groups' sums stay below 2^16 for d <= 16). The even and odd
+//     pair words are kept in two planes, so a lane that owns outputs 2m and 2m+1 of a trial
+//     reads one word, and consecutive lanes read consecutive words. The classes depend on the
+//     delay table only, so the plan computes them once (tiled_plan, below) as one fixed-size
+//     table per (trial tile, stage), together with a balanced split of the stage's word building
+//     over the warps; the kernel never searches for them.
 //   * TMA brings each stage's 16 channel rows (one 3-D tensor copy: every row from the same
 //     128-byte segment on, so each lands contiguous) and its class table into shared memory
 //     NS - 1 stages ahead (NS = 4 staging buffers, or 3 where 4 do not fit shared memory);
 //     completion is tracked by mbarriers with bounded waits.
-//   * The main loop adds one pattern word per (trial, sample) with one DP2A: one 32-bit
-//     shared-memory load per eight channel-adds, for uint8 and uint16 (decimated) data alike.
+//   * The main loop adds, per (trial, output pair), the two groups' pair words with one IADD
+//     and splits the sum over the two outputs with two DP2As: one 32-bit shared-memory load per
+//     sixteen channel-adds, for uint8 and uint16 (decimated) data alike.
 //
 // Software pipeline, one __syncthreads per stage s:
 //     TMA for stage s+NS-1 | build the words of stage s+1 | accumulate stage s
-// Words are built from 32-bit loads and funnel shifts; the four-channel sums are formed in SWAR
+// Words are built from 32-bit loads and funnel shifts; the eight-channel sums are formed in SWAR
 // lanes (bytes split into 16-bit lanes for uint8 data). Where each class's channel rows start in
 // a stage buffer (row word and funnel shift) depends on where the stage's copy starts, so the
 // CTA works it out once per stage, one (class, channel) per thread, two stages ahead. Exact
@@ -44,7 +48,7 @@ constexpr int kTileTrials = 64;
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTPW = kTileTrials / kWarps;  // trials per warp
-constexpr int kG = 8;                       // channels per group (one pattern word)
+constexpr int kG = 8;                       // channels per group (one delay class)
 constexpr int kNG = 2;                      // groups per stage
 constexpr int kRows = kG * kNG;             // channel rows per stage
 constexpr int kMaxNStage = 4;               // staging buffers (rows + class table), at most
@@ -54,7 +58,7 @@ constexpr int kSegBytes = 128;              // inner extent of a staged-row copy
 constexpr size_t kSmemLimit = 220 * 1024;   // dynamic shared memory a CTA may plan for
 
 // One delay class: its channels' first staged sample relative to the tile's first trial
-// (rel), and its words in the stage's pattern-word region.
+// (rel), and its pair words in the stage's word region.
 struct ClsEntry {
   int16_t rel[kG];
   int16_t zoff;  // first word (multiple of 4)
@@ -68,7 +72,7 @@ struct GroupTab {
   int32_t ncls, pad0, pad1, pad2;
 };
 
-// The stage's pattern-word build, cut at plan time into blocks of 32 units (one per lane) and
+// The stage's pair-word build, cut at plan time into blocks of 32 units (one per lane) and
 // dealt to the warps in near-equal contiguous shares. A share is a few ranges, each within one
 // class: group << 4 | class, first block << 8, blocks << 16.
 struct StageTab {
@@ -256,71 +260,81 @@ struct RowItem {
   uint32_t sh[kG];
 };
 
-// Row word of channel k at byte offset OFF, shifted to the class's first sample (the funnel
-// shift uses the low 5 bits of its amount).
-template <int OFF>
-__device__ __forceinline__ uint32_t row_word(const RowItem& it, int k) {
-  return __funnelshift_r(lds<OFF>(it.addr[k]), lds<OFF + 4>(it.addr[k]), it.sh[k]);
-}
-
 template <typename T>
 struct Word;
 
-// uint8 data: pattern word = (sum of channels 0-3) | (sum of channels 4-7) << 16 of one sample.
-// A lane builds units u and u + 32 (pattern words 4u .. 4u + 3 and 4u + 128 .. 4u + 131), each
-// from two row words per channel; lanes take consecutive units, so every load and store is
-// free of bank conflicts. Bytes are split into even/odd 16-bit lanes so that four channels add
-// without carries, then the two four-channel sums of each sample are paired into its word.
+// Row words of channel k at byte offset OFF: the word holding the class's first sample and the
+// next one.
+template <int OFF>
+__device__ __forceinline__ void row_words(const RowItem& it, int k, uint32_t& w0, uint32_t& w1) {
+  w0 = lds<OFF>(it.addr[k]);
+  w1 = lds<OFF + 4>(it.addr[k]);
+}
+
+// uint8 data. A lane builds units u and u + 32; unit u covers pair words 4u .. 4u + 3, i.e.
+// the eight-channel sums S[4u .. 4u + 4] (one more than its words, which the last pair word
+// needs). Each channel's two row words are funnel-shifted to the class's first sample; bytes
+// are split into even/odd 16-bit lanes so that eight channels add without carries (8 x 255 <
+// 2^16), and the fifth sample, byte (shift / 8) of the second row word, is added by a DP4A on
+// the rotated word. The pair words go to the class's even plane (4u, 4u + 2) and odd plane
+// (4u + 1, 4u + 3); lanes take consecutive units, so every load and store is free of bank
+// conflicts.
 template <>
 struct Word<uint8_t> {
-  static constexpr int kUnit = 4;  // pattern words per unit
+  static constexpr int kUnit = 4;  // pair words per unit
   template <int OFF>
-  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* dst) {
-    uint32_t elo = 0, olo = 0, ehi = 0, ohi = 0;
+  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* ev, uint32_t* od) {
+    uint32_t e = 0, o = 0, s4 = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t a = row_word<OFF>(it, k), b = row_word<OFF>(it, k + 4);
-      elo += a & 0x00FF00FFu;            // samples 0, 2
-      olo += __byte_perm(a, 0, 0x4341);  // samples 1, 3
-      ehi += b & 0x00FF00FFu;
-      ohi += __byte_perm(b, 0, 0x4341);
+    for (int k = 0; k < kG; ++k) {
+      uint32_t w0, w1;
+      row_words<OFF>(it, k, w0, w1);
+      const uint32_t a = __funnelshift_r(w0, w1, it.sh[k]);  // samples 0..3 in bytes 0..3
+      e += a & 0x00FF00FFu;                                  // samples 0, 2
+      o += __byte_perm(a, 0, 0x4341);                        // samples 1, 3
+      s4 = __dp4a(__funnelshift_r(w1, w1, it.sh[k]), 1u, s4);  // sample 4
     }
-    uint4 o;
-    o.x = __byte_perm(elo, ehi, 0x5410);  // sample 0: (ch0-3 sum) | (ch4-7 sum) << 16
-    o.y = __byte_perm(olo, ohi, 0x5410);  // sample 1
-    o.z = __byte_perm(elo, ehi, 0x7632);  // sample 2
-    o.w = __byte_perm(olo, ohi, 0x7632);  // sample 3
-    *reinterpret_cast<uint4*>(dst) = o;
+    uint2 x, y;
+    x.x = __byte_perm(e, o, 0x5410);   // S0 | S1 << 16
+    x.y = __byte_perm(e, o, 0x7632);   // S2 | S3 << 16
+    y.x = __byte_perm(o, e, 0x7610);   // S1 | S2 << 16
+    y.y = __byte_perm(o, s4, 0x5432);  // S3 | S4 << 16
+    *reinterpret_cast<uint2*>(ev) = x;
+    *reinterpret_cast<uint2*>(od) = y;
   }
 };
 
-// uint16 data: a lane builds units u and u + 32 (pattern words 2u, 2u + 1 and 2u + 64, 2u + 65)
-// from two row words per channel; 16-bit lanes add four channels without carries
-// (4 x 255 x d < 2^16).
+// uint16 data. Unit u covers pair words 2u, 2u + 1 (sums S[2u .. 2u + 2]) from two row words
+// per channel; 16-bit lanes add eight channels without carries (8 x 255 x d < 2^16), and the
+// third sample, halfword (shift / 16) of the second row word, is added by a DP2A on the
+// rotated word.
 template <>
 struct Word<uint16_t> {
   static constexpr int kUnit = 2;
   template <int OFF>
-  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* dst) {
-    uint32_t lo = 0, hi = 0;
+  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* ev, uint32_t* od) {
+    uint32_t e = 0, s2 = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      lo += row_word<OFF>(it, k);      // samples 0, 1 of channels 0-3
-      hi += row_word<OFF>(it, k + 4);  // of channels 4-7
+    for (int k = 0; k < kG; ++k) {
+      uint32_t w0, w1;
+      row_words<OFF>(it, k, w0, w1);
+      e += __funnelshift_r(w0, w1, it.sh[k]);                  // samples 0, 1
+      s2 = __dp2a_lo(__funnelshift_r(w1, w1, it.sh[k]), 1u, s2);  // sample 2
     }
-    uint2 o;
-    o.x = __byte_perm(lo, hi, 0x5410);  // sample 0
-    o.y = __byte_perm(lo, hi, 0x7632);  // sample 1
-    *reinterpret_cast<uint2*>(dst) = o;
+    *ev = e;                           // S0 | S1 << 16
+    *od = __byte_perm(e, s2, 0x5432);  // S1 | S2 << 16
   }
 };
 
-__device__ __forceinline__ uint32_t dot(uint32_t z, uint32_t acc) {
-  return __dp2a_lo(z, 0x0101u, acc);  // acc + (ch0-3 sum) + (ch4-7 sum)
+// Add one pair word (S[u] | S[u + 1] << 16, or the sum of two groups' words) to the two
+// outputs it serves.
+__device__ __forceinline__ void pair_add(uint32_t z, uint32_t& even, uint32_t& odd) {
+  even = __dp2a_lo(z, 0x0001u, even);  // + low half
+  odd = __dp2a_lo(z, 0x0100u, odd);    // + high half
 }
 
-// Build every pattern word of one stage: warp w walks its ranges of the plan's work list; lane
-// l builds unit 32 * b + l of every block b of a range, two blocks per pass.
+// Build every pair word of one stage: warp w walks its ranges of the plan's work list; lane l
+// builds unit 32 * b + l of every block b of a range, two blocks per pass.
 template <typename T>
 __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& at, uint32_t rawb,
                                             uint32_t* Zs, int warp, int lane) {
@@ -349,14 +363,18 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
       it.sh[k] = sv.x >> (8 * k);
       it.sh[k + 4] = sv.y >> (8 * k);
     }
-    uint32_t* dst = Zs + tb.g[gi].cls[p].zoff + U * u;
+    // even plane: pair words 0, 2, 4, ... of the class; odd plane: 1, 3, 5, ...
+    uint32_t* ev = Zs + tb.g[gi].cls[p].zoff + (U / 2) * u;
+    uint32_t* od = ev + zlen / 2;
     for (int b = 0; b < nb; b += 2) {
-      if (u * U < zlen) Word<T>::template unit<0>(it, dst);
-      if (b + 1 < nb && (u + 32) * U < zlen) Word<T>::template unit<128>(it, dst + 32 * U);
+      if (u * U < zlen) Word<T>::template unit<0>(it, ev, od);
+      if (b + 1 < nb && (u + 32) * U < zlen)
+        Word<T>::template unit<128>(it, ev + 16 * U, od + 16 * U);
 #pragma unroll
       for (int k = 0; k < kG; ++k) it.addr[k] += 256u;  // 64 units further
       u += 64;
-      dst += 64 * U;
+      ev += 32 * U;
+      od += 32 * U;
     }
   }
 }
@@ -364,7 +382,8 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
 template <typename T, int TT, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_dedisp_tiled(const __grid_constant__ TiledArgs a) {
-  constexpr int KT = TT / 32;
+  constexpr int KT = TT / 32;  // outputs per lane and trial
+  constexpr int KP = TT / 64;  // pair words per lane and trial
   extern __shared__ __align__(1024) unsigned char smem[];  // tensor copies land 128-aligned
   const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap, NS);
   T* raw = reinterpret_cast<T*>(smem + SL.raw);
@@ -438,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (s + 2 < nstages) addr_entry<T>(a, ain, j0, tid, &atab[s & 1]);
       ain = addr_inputs(a, s + 3, nstages, ngroups, trial0, tid);
     }
-    // (2) pattern words of stage s + 1
+    // (2) pair words of stage s + 1
     bool ok = true;
     if (s + 1 < nstages) {
       const int b1 = (s + 1) % NS;
@@ -447,21 +466,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         build_stage<T>(tab[b1], atab[(s + 1) & 1], smem_addr(raw + (size_t)b1 * stage_elems),
                        Zbuf + (size_t)((s + 1) & 1) * a.zcap, warp, lane);
     }
-    // (3) accumulate stage s
+    // (3) accumulate stage s: lane l of the warp reads, for each of its trials, pair word
+    //     l + 32k of the trial's plane in both groups (outputs 2(l + 32k) and 2(l + 32k) + 1)
     {
       const StageTab& tc = tab[s % NS];
       const uint32_t* Zs = Zbuf + (size_t)(s & 1) * a.zcap + lane;
+      const uint32_t* zp[kTPW];
+      const uint32_t* zq[kTPW];
 #pragma unroll
-      for (int g = 0; g < kNG; ++g) {
-        if (g < ng) {  // uniform; only the last stage may hold fewer groups
-          const uint32_t* zp[kTPW];
+      for (int q = 0; q < kTPW; ++q) {
+        zp[q] = Zs + tc.g[0].zstart[warp + kWarps * q];
+        zq[q] = Zs + tc.g[1].zstart[warp + kWarps * q];
+      }
+      if (ng == kNG) {  // uniform; only the last stage may hold one group
 #pragma unroll
-          for (int q = 0; q < kTPW; ++q) zp[q] = Zs + tc.g[g].zstart[warp + kWarps * q];
+        for (int k = 0; k < KP; ++k)
 #pragma unroll
-          for (int k = 0; k < KT; ++k)
+          for (int q = 0; q < kTPW; ++q)
+            pair_add(zp[q][32 * k] + zq[q][32 * k], acc[q][2 * k], acc[q][2 * k + 1]);
+      } else {
 #pragma unroll
-            for (int q = 0; q < kTPW; ++q) acc[q][k] = dot(zp[q][32 * k], acc[q][k]);
-        }
+        for (int k = 0; k < KP; ++k)
+#pragma unroll
+          for (int q = 0; q < kTPW; ++q) pair_add(zp[q][32 * k], acc[q][2 * k], acc[q][2 * k + 1]);
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -488,15 +515,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       int32_t* yr = a.y + (int64_t)(trial0 + t) * a.y_stride;
       unsigned long long s1 = 0, lo = 0, hi = 0;
 #pragma unroll
-      for (int k = 0; k < KT; ++k) {
-        const int64_t j = j0 + lane + 32 * k;
-        if (j < a.nout) {
-          const uint32_t v = acc[q][k];
-          yr[j] = (int32_t)v;
-          s1 += v;
-          const unsigned long long sq = (unsigned long long)v * v;
-          lo += sq;
-          hi += (lo < sq) ? 1ull : 0ull;
+      for (int k = 0; k < KP; ++k) {
+        const int64_t j = j0 + 2 * (lane + 32 * k);
+        if (j + 1 < a.nout)
+          *reinterpret_cast<int2*>(yr + j) = make_int2((int32_t)acc[q][2 * k],
+                                                       (int32_t)acc[q][2 * k + 1]);
+        else if (j < a.nout)
+          yr[j] = (int32_t)acc[q][2 * k];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (j + h < a.nout) {
+            const uint32_t v = acc[q][2 * k + h];
+            s1 += v;
+            const unsigned long long sq = (unsigned long long)v * v;
+            lo += sq;
+            hi += (lo < sq) ? 1ull : 0ull;
+          }
         }
       }
 #pragma unroll
@@ -545,7 +579,7 @@ cudaError_t prepare_t(size_t smem) {
 
 namespace {
 
-// Cut a stage's classes into blocks of 32 units (U pattern words each) and deal them to the
+// Cut a stage's classes into blocks of 32 units (U pair words each) and deal them to the
 // warps in contiguous shares of ceil(blocks / warps); false if a share needs more ranges than
 // a warp's list holds or a class more blocks than a range can name.
 bool deal_work(StageTab& st, int U) {
@@ -601,16 +635,19 @@ int tiled_tile_samples(int is_u16, int choice) {
 }
 
 // Host: delay classes of every (trial tile, stage) of one range, as the kernel reads them.
-// Classes are numbered in order of their first trial; a class's words start at a multiple of 4
-// within the stage, groups one after another. Fails (ok = false) where the kernel's limits do
-// not hold: a 16-bit lane sums four channels of values up to 255 x decimation, so decimation
-// must stay at or below 64; delays must be monotone in the trial within a channel; classes,
-// items and the staged rows must fit their fixed-size tables and shared memory.
+// Classes are numbered in order of their first trial; a class's zlen pair words start at a
+// multiple of 4 within the stage, groups one after another, the even plane (pair words 0, 2,
+// 4, ...) in the first zlen / 2 words and the odd plane after it. A trial whose sequence starts
+// o words into its class reads plane (o mod 2) from word o / 2 on. Fails (ok = false) where the
+// kernel's limits do not hold: a 16-bit lane holds the sum of two groups' eight channels of
+// values up to 255 x decimation, so decimation must stay at or below 16; delays must be
+// monotone in the trial within a channel; classes, work lists and the staged rows must fit
+// their fixed-size tables and shared memory.
 TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int tt) {
   TiledPlan P;
   P.ok = false;
   const bool u16 = decimation > 1;
-  if (decimation < 1 || 4 * 255 * decimation > 65535 || cpad % kG) return P;
+  if (decimation < 1 || kRows * 255 * decimation > 65535 || cpad % kG) return P;
   const int D = kTileTrials, NG = kNG, U = u16 ? 2 : 4;
   const int ngroups = cpad / kG, nstages = (ngroups + NG - 1) / NG;
   const int ntiles = (ntr + D - 1) / D;
@@ -667,7 +704,7 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
           }
           cls_of[i] = p;
         }
-        int zoff[kMaxCls];
+        int zoff[kMaxCls], zlens[kMaxCls];
         for (int p = 0; p < ncls; ++p) {
           const int zlen = (tt + cmax[p] - cmin[p] + 3) & ~3;
           zoff[p] = words;
@@ -679,11 +716,14 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
           }
           e.zoff = (int16_t)words;
           e.zlen = (int16_t)zlen;
+          zlens[p] = zlen;
           words += zlen;
           if (words > 32767) return P;
         }
-        for (int i = 0; i < n; ++i)
-          gt.zstart[i] = (int16_t)(zoff[cls_of[i]] + b[i] - cmin[cls_of[i]]);
+        for (int i = 0; i < n; ++i) {
+          const int p = cls_of[i], o = b[i] - cmin[p];
+          gt.zstart[i] = (int16_t)(zoff[p] + (o % 2) * (zlens[p] / 2) + o / 2);
+        }
         gt.ncls = ncls;
       }
       if (!deal_work(st, U)) return P;
@@ -720,8 +760,9 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
 
 // Host: plan one range and verify the tables against the delay table they were built from,
 // independently of how they were built. Returns the number of violations of:
-//   - every trial's word sequence lies inside its class's words, and word u of the class adds,
-//     in every channel of the group, the sample at the trial's own delay (rel + offset);
+//   - every trial's tt / 2 pair words lie inside one plane of its class, and the class word
+//     they stand for (o = 2 x plane position + plane) adds, in every channel of the group, the
+//     sample at the trial's own delay (rel + o);
 //   - class word ranges start and end on 16-byte boundaries;
 //   - the stage's copy start is the smallest first-trial delay of its rows, and every read of
 //     every trial stays inside the staged row;
@@ -777,10 +818,18 @@ int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, 
         for (int p = 0; p < gt.ncls; ++p) bad += (gt.cls[p].zoff % 4) + (gt.cls[p].zlen % 4) != 0;
         for (int i = 0; i < n; ++i) {
           const int z = gt.zstart[i];
-          int p = 0;
-          while (p < gt.ncls &&
-                 !(gt.cls[p].zoff <= z && z + tt <= gt.cls[p].zoff + gt.cls[p].zlen))
-            ++p;
+          int p = 0, o = -1;
+          for (; p < gt.ncls; ++p) {
+            const int zo = gt.cls[p].zoff, half = gt.cls[p].zlen / 2;
+            if (zo <= z && z + tt / 2 <= zo + half) {
+              o = 2 * (z - zo);  // even plane
+              break;
+            }
+            if (zo + half <= z && z + tt / 2 <= zo + 2 * half) {
+              o = 2 * (z - zo - half) + 1;  // odd plane
+              break;
+            }
+          }
           if (p == gt.ncls) {
             ++bad;
             continue;
@@ -788,7 +837,7 @@ int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, 
           for (int q = 0; q < kG; ++q) {
             const int64_t want = (int64_t)tab[(int64_t)(t0 + i) * cpad + c0 + q] -
                                  tab[(int64_t)t0 * cpad + c0 + q];
-            bad += (int64_t)gt.cls[p].rel[q] + (z - gt.cls[p].zoff) != want;
+            bad += (int64_t)gt.cls[p].rel[q] + o != want;
           }
         }
       }

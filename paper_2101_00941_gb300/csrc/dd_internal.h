@@ -73,7 +73,7 @@ struct TiledArgs {
   int32_t n_trials;
   int32_t cpad;
   int32_t row_slot;        // elements per staged channel row
-  int32_t zcap;            // pattern words per stage
+  int32_t zcap;            // pair words per stage buffer
   int32_t nstage;          // staging buffers (3 or 4)
   const uint8_t* tabs;     // delay-class tables of the range, one per (trial tile, stage)
   int32_t* err;            // bit 0: a bounded wait ran out

@@ -216,7 +216,7 @@ cudaError_t launch_dedisp_naive(const DedispRange& r, int32_t cpad, cudaStream_t
 }
 
 // Direct kernel: the fallback for ranges the tiled kernel cannot take (delay classes beyond
-// its tables, as with coarse channels, or decimation above x64). A CTA of 8 warps owns 16
+// its tables, as with coarse channels, or decimation above x16). A CTA of 8 warps owns 16
 // consecutive trials x 512 outputs; a warp takes 2 trials, lane l the 4-sample groups
 // 4l + 128g (g = 0..3) of both. Per channel a lane reads, through the read-only cache, the two
 // aligned 32-bit words holding its 4 samples and funnel-shifts them into place (the shift is

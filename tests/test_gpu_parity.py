@@ -166,16 +166,16 @@ def _tiled_regime(nchans=1001, nsamp=1 << 15):
 
 def test_kernel_choice():
     """Ranges whose delay classes fit the tiled kernel's tables run on it (512-sample tiles);
-    x128 decimation (four channels of 255 x 128 do not fit a 16-bit lane) and the tiny
-    workload's 64 coarse channels (up to 63 classes per group) run on the direct kernel, and
-    DD_FLAG_NAIVE selects the one-thread-per-output kernel."""
+    x32 .. x128 decimation (two groups' eight channels of 255 x d do not fit a 16-bit lane)
+    and the tiny workload's 64 coarse channels (up to 63 classes per group) run on the direct
+    kernel, and DD_FLAG_NAIVE selects the one-thread-per-output kernel."""
     w = _tiled_regime()
     plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1)
     try:
         got = [plan.kernel(r) for r in range(len(w.ranges))]
     finally:
         plan.close()
-    assert got == [(dd.DD_KERNEL_TILED, 512)] * 7 + [(dd.DD_KERNEL_DIRECT, 0)]
+    assert got == [(dd.DD_KERNEL_TILED, 512)] * 5 + [(dd.DD_KERNEL_DIRECT, 0)] * 3
     t = configs.tiny()
     plan = dd.Plan(t.freqs(), t.tsamp, t.ranges_array(), 4096, n_streams=1)
     try:
@@ -279,6 +279,24 @@ def test_tiled_kernel_256_sample_tiles():
         plan.close()
     x = w.generate(_arrivals(w))
     assert check(w, x, [4096] * 3 + [2048], 2, flags=dd.DD_FLAG_TILE256) >= 0
+
+
+def test_tiled_kernel_odd_output_counts():
+    """Windows of odd length: x1 ranges only, so the overlap is the largest delay (63 samples),
+    and chunks of 4096, 4096, 2047 and 1001 samples give windows of 4033, 4096, 2047 and 1001
+    outputs. The tiled kernel writes a lane's outputs in pairs; the last output of an odd window
+    is written, and counted in the moments, alone."""
+    w = _tiled_regime(nsamp=1 << 14)
+    w.ranges = (configs.DMRange(0.0, 0.0625, 70, 1), configs.DMRange(4.375, 0.0625, 3, 1))
+    sizes = [4096, 4096, 2047, 1001]
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1)
+    try:
+        assert plan.O == 63
+        assert [plan.kernel(r)[0] for r in range(2)] == [dd.DD_KERNEL_TILED] * 2
+    finally:
+        plan.close()
+    x = w.generate(_arrivals(w))
+    assert check(w, x[:sum(sizes)], sizes, 2) >= 0
 
 
 def test_one_thread_per_output_kernel_matches():

@@ -44,8 +44,8 @@ def test_8192_channel_plan_edges():
 
 
 def test_ragged_channels_and_trial_tiles():
-    """1001 channels (padded to 1008) and ranges of 150, 75, 130, 70, 40, 30, 20 trials; x128
-    decimation does not fit a pattern word's 16-bit lanes."""
+    """1001 channels (padded to 1008) and ranges of 150, 75, 130, 70, 40, 30, 20, 10 trials;
+    above x16 the sum of two groups' eight channels does not fit a pair word's 16-bit lanes."""
     ranges = (configs.DMRange(0.0, 0.0625, 150, 1), configs.DMRange(9.375, 0.125, 75, 2),
               configs.DMRange(18.75, 0.15625, 130, 4), configs.DMRange(39.0625, 0.3125, 70, 8),
               configs.DMRange(60.9375, 0.625, 40, 16), configs.DMRange(85.9375, 1.25, 30, 32),
@@ -55,7 +55,7 @@ def test_ragged_channels_and_trial_tiles():
     for tab, r in zip(_tables(w), w.ranges):
         ok, bad = dd.dd_tiled_plan_check(tab, r.decimation, 512)
         assert bad == 0
-        assert ok == (1 if r.decimation <= 64 else 0), r
+        assert ok == (1 if r.decimation <= 16 else 0), r
 
 
 def test_odd_group_count():
