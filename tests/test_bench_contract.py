@@ -51,3 +51,29 @@ def test_gpu_arm_line():
     assert r["bound"] == "alu" and 0 < r["frac"] < 1.5 and r["peak"] > 0
     assert r["traffic"] and r["traffic"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_metric_counts_the_outputs_of_the_chunk_windows():
+    """The benchmark's DM-trial·samples per step (sum over ranges of n_r * (N - O) / d_r) equals
+    the outputs of the step's eight chunk windows as the oracle lays them out, and the adds are
+    one per channel per output."""
+    import oracle
+    from synth import configs
+    bench = _bench_module()
+    w = configs.mid()
+    ranges = w.ranges_array()
+    O = oracle.overlap(oracle.shift_tables(w.freqs(), w.tsamp, ranges), ranges)
+    sizes = [w.chunk_len] * (w.nsamp // w.chunk_len)
+    produced = sum(int(r[2]) * (hi // int(r[3]) - lo // int(r[3]))
+                   for (_, _, lo, hi) in oracle.chunk_windows(sizes, O) for r in ranges)
+    assert O == 14496
+    assert bench.outputs_per_pass(w, O) == produced
+    assert bench.adds_per_pass(w, O) == produced * 4096
