@@ -1,24 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark: streamed brute-force dedispersion + boxcar single-pulse search on GB300.
 
-One step = the whole hot path over one synthetic beam of the 4096-channel
-workload (1250-1550 MHz, 64 us, 2^20 uint8 samples = 4.3 GB, 4050 DM trials
-over 0-1000 pc cm^-3 with x1/x2/x4/x8 decimation, boxcars 1..256, 6 sigma):
-eight 2^17-sample chunks over four CUDA streams, each chunk corner-turned,
-decimated, dedispersed, searched, and its candidates copied to the host.
+Default workload (the out-of-core beam): 8192 channels over 1000-1500 MHz, 50 us sampling,
+2^25 uint8 samples (275 GB, more than the GPU's memory), 6050 DM trials over 0-3000 pc cm^-3
+with x1/x2/x4/x8/x16 decimation, boxcars 1..512 at 6 sigma. One step = the whole beam: 64 chunks
+of 2^19 samples over 4 CUDA streams, each chunk corner-turned, decimated, dedispersed, searched
+and its candidates copied to the host. The input is a ring of 8 distinct seeded 2^19-sample
+chunks (4.3 GB each), reused cyclically to make up the 2^25 samples.
 
-  value : DM-trial*samples/s with the input already resident in HBM
-  e2e   : the same through the C ABI from pinned HOST memory (H2D inside the step)
-Timing: CUDA events around each step with a device synchronize on both sides;
-W warm-up steps; the 4.3 GB input is larger than L2 (no flush needed).
+  value : DM-trial*samples/s with the ring resident in HBM
+  e2e   : the same through the C ABI from the ring in pinned HOST memory (H2D inside the step)
+
+`--workload mid` is the 4096-channel, 2^20-sample beam (4050 trials over 0-1000, x1..x8, 8 chunks
+of 2^17 over 4 streams); serve, batch, transfer and peaks are the other workloads.
+Timing: CUDA events around the timed steps with a device synchronize on both sides, W warm-up
+steps; every chunk (4.3 GB) is larger than L2, so no flush is needed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-For N > 1 launch with torchrun: one independent beam per rank (weak scaling),
-max of the per-rank step times.
+For N > 1 launch with torchrun: one independent beam per rank (weak scaling), max of the
+per-rank step times.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -36,12 +41,10 @@ from synth import configs  # noqa: E402
 
 METRIC = "DM-trial·samples/s dedispersed"
 UNIT = "DM-trial·samples/s"
-# Integer ALU roofline: 152 SMs x 128 int32 lanes per clock (ALU + FMA pipes) x 2070 MHz.
-ALU_PEAK_ADDS = 152 * 128 * 2070e6
-# DRAM bytes (read + write) of the four dedispersion launches of one full 131072-sample chunk
-# window of the 4096-channel workload, from one ncu capture of the current kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_dedisp_tiled_mid_4096ch.md).
-DEDISP_DRAM_BYTES_PER_FULL_CHUNK = 1.312e9 + 0.791e9 + 0.386e9 + 0.196e9
+# DRAM bytes per output sample of the dedispersion launches, from one ncu capture; valid only
+# for the kernel source it was taken on (its SHA-256 is stored beside the figure)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dedisp_dram_traffic.json")
+DEDISP_SOURCE = os.path.join(ROOT, "paper_2101_00941_gb300", "csrc", "dd_dedisp.cu")
 
 
 def dist_info():
@@ -60,16 +63,6 @@ def rank_max(values, device):
     if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
     return [float(v) for v in t.cpu()]
-
-
-def outputs_per_pass(w, O: int) -> int:
-    """DM-trial*samples produced from one beam: sum_r n_r * (N - O) / d_r."""
-    return sum(r.n_trials * ((w.nsamp - O) // r.decimation) for r in w.ranges)
-
-
-def adds_per_pass(w, O: int) -> int:
-    """Algorithmic adds of brute-force dedispersion: one per channel per output sample."""
-    return outputs_per_pass(w, O) * w.nchans
 
 
 def pulse_offsets(w):
@@ -140,13 +133,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_input(w, pinned: bool):
-    import torch
-    x = torch.empty((w.nsamp, w.nchans), dtype=torch.uint8, pin_memory=pinned)
-    w.generate(pulse_offsets(w), out=x.numpy())
-    return x
-
-
 def run_step(plan, chunks, w, lat=None):
     """Enqueue every chunk (4-deep pipeline over the plan's streams) and collect candidates."""
     import paper_2101_00941_gb300 as dd
@@ -192,18 +178,44 @@ def time_steps(plan, chunks, w, steps, warmup, barrier, lat=None):
     return ms, ncand, launches, dd_ms, dd_n
 
 
-def cpu_baseline(w, x_np, O, target_s: float = 15.0):
+def stream_workload(name: str, nsamp: int | None = None, beam: int = 0, streams: int = 4):
+    """(workload, chunks in the input ring) of a streamed workload: the out-of-core beam (8192
+    channels, DM 0-3000) or the 4096-channel beam (DM 0-1000)."""
+    if name == "ooc":
+        L = 1 << 19
+        ring = 8
+        # pulses are drawn over the ring's samples so that they land in it
+        w = configs.out_of_core(nsamp=ring * L)
+        w.beam = beam
+        w.nsamp = nsamp or (1 << 25)
+        w.name = f"ooc_8192ch_{w.nsamp}"
+        w.chunk_len, w.n_streams = L, streams
+        return w, min(ring, w.nsamp // L)
+    w = configs.mid(beam=beam, nsamp=nsamp or (1 << 20), n_streams=streams)
+    return w, w.nsamp // w.chunk_len
+
+
+def baseline_window(w, O):
+    """(first global sample, samples) of the CPU baseline's input: one window of up to 65536
+    outputs starting where the second chunk's window starts (L - O), with the O samples of
+    history its outputs read."""
+    L = w.chunk_len
+    win = min(L, 1 << 16)
+    return L - O, O + win
+
+
+def cpu_baseline(w, x_win, t_in0, O, target_s: float = 15.0):
     """The oracle, as it stands, on a bounded sample of the same workload: every range, a few
-    trials spread over the range, over one full chunk window. Returns DM-trial*samples/s."""
+    trials spread over the range, over one window of up to 65536 samples with full history.
+    x_win holds global samples [t_in0, t_in0 + len); t_in0 = L - O. Returns DM-trial*samples/s."""
     import oracle
     oracle.build()
     f = w.freqs()
     ranges = w.ranges_array()
     tabs = oracle.shift_tables(f, w.tsamp, ranges)
-    k = 1  # second chunk: a full window with history
-    T = k * w.chunk_len
-    lo, hi = T - O, T + w.chunk_len - O
-    ntr = 16  # at least one trial per host thread in the oracle's parallel loops
+    lo = t_in0
+    hi = t_in0 + x_win.shape[0] - O
+    ntr = 8
     done_out, elapsed = 0, 0.0
     while elapsed < target_s and ntr <= 4096:
         t0 = time.perf_counter()
@@ -212,7 +224,7 @@ def cpu_baseline(w, x_np, O, target_s: float = 15.0):
             d = int(ranges[r][3])
             tr = np.linspace(0, tab.shape[0] - 1, min(ntr, tab.shape[0])).astype(np.int32)
             J0, J1 = lo // d, hi // d
-            xd = oracle.decimate(x_np, 0, d, J0, J1 - J0 + int(tab.max()))
+            xd = oracle.decimate(x_win, t_in0, d, J0, J1 - J0 + int(tab.max()))
             y = oracle.dedisperse(xd, J0, tab, tr, J0, J1 - J0)
             oracle.sps(y, tr, r, d, J0, oracle.widths_for_range(w.widths, d), 32, w.threshold)
             outs += tr.size * (J1 - J0)
@@ -221,30 +233,32 @@ def cpu_baseline(w, x_np, O, target_s: float = 15.0):
         if dt * 4 > target_s:
             break
         ntr *= 4
-    return {"value": done_out / elapsed, "unit": UNIT, "cores": min(os.cpu_count(), ntr),
+    per_range = "/".join(str(r.n_trials) for r in w.ranges)
+    return {"value": done_out / elapsed, "unit": UNIT, "cores": os.cpu_count(),
             "kind": "oracle",
-            "sample": f"{done_out} DM-trial*samples: {ntr} trials per range (of 1500/750/800/1000) "
-                      f"over one full {w.chunk_len}-sample chunk window, dedispersion + search, "
+            "sample": f"{done_out} DM-trial*samples: {ntr} trials per range (of {per_range}) over "
+                      f"a {hi - lo}-sample window with full history, dedispersion + search, "
                       f"{elapsed:.1f} s"}
 
 
 def main_reference(args):
+    """The reference arm: the CPU oracle timed on the host cores on this arm's workload, each
+    step a bounded sample of it (rank 0 only)."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    w = configs.mid()
+    w, nring = stream_workload(args.workload if args.workload in ("mid", "ooc") else "ooc")
     import oracle
     f = w.freqs()
     O = oracle.overlap(oracle.shift_tables(f, w.tsamp, w.ranges_array()), w.ranges_array())
-    # host input only: two chunks of samples are enough for a one-chunk-window sample
-    n = 2 * w.chunk_len + w.chunk_len
-    x = w.generate(pulse_offsets(w), nsamp=n)
+    t_in0, n = baseline_window(w, O)
+    x = w.generate(pulse_offsets(w), t0=t_in0, nsamp=n)
     for _ in range(args.warmup):
-        cpu_baseline(w, x, O, target_s=2.0)
+        cpu_baseline(w, x, t_in0, O, target_s=2.0)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(w, x, O, target_s=8.0))
+        vals.append(cpu_baseline(w, x, t_in0, O, target_s=8.0))
     wall = time.perf_counter() - t0
     value = float(np.mean([v["value"] for v in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
@@ -438,70 +452,6 @@ def batch_workload(args):
     return 0
 
 
-def ooc_workload(args):
-    """The out-of-core shape: 8192 channels over 1000-1500 MHz, 50 us, DM 0-3000 with x1..x16
-    decimation (6050 trials, overlap ~138k samples), 2^19-sample chunks over 4 streams, input in
-    pageable host memory. One step = --ooc-chunks chunks of one continuing stream (a pool of two
-    distinct seeded chunks, reused). Three ways in: pageable through the pinned staging threads
-    (Sec. 2.1; the headline), pageable through the CUDA driver, and pinned host memory."""
-    import torch
-
-    import paper_2101_00941_gb300 as dd
-    torch.cuda.set_device(0)
-    dev = torch.cuda.current_device()
-    dd.build()
-    L = 1 << 19
-    w = configs.out_of_core(nsamp=2 * L)
-    w.chunk_len, w.n_streams = L, 4
-    x = np.empty((2 * L, w.nchans), dtype=np.uint8)  # pageable
-    w.generate(pulse_offsets(w), out=x)
-    pool = [x[:L], x[L:]]
-    nchunks = args.ooc_chunks
-    per_chunk = sum(r.n_trials * (L // r.decimation) for r in w.ranges)  # full windows
-    res = {}
-    for mode in ("staged", "driver", "pinned"):
-        plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=w.n_streams,
-                       max_width=max(w.widths), device=dev,
-                       staging_threads=4 if mode == "staged" else 0)
-        src = [torch.from_numpy(c).pin_memory() for c in pool] if mode == "pinned" else pool
-        chunks = [src[k % 2] for k in range(nchunks)]
-        # the first chunk of the stream fills the overlap; it runs before the timed steps
-        plan.run(chunks[0], L)
-        plan.search(w.widths, w.threshold)
-        plan.sync()
-        with ClockSampler(dev) as clk:
-            ms, ncand, launches, _, _ = time_steps(plan, chunks, w, args.steps, args.warmup,
-                                                   lambda: None)
-        plan.close()
-        del src
-        res[mode] = {"value": per_chunk * nchunks * args.steps / (ms * 1e-3),
-                     "ms_per_step": ms / args.steps, "candidates_per_step": ncand / args.steps,
-                     "real_time_factor": nchunks * L * w.tsamp / (ms * 1e-3 / args.steps),
-                     "gpu_launches": launches, "clocks": clk.summary()}
-    head = res["staged"]
-    line = {
-        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32",
-        "data": "synthetic",
-        "config": {"workload": "ooc_8192ch_2e19_chunks", "nchans": w.nchans, "tsamp_us": 50.0,
-                   "trials": w.n_trials, "chunk_len": L, "chunks_per_step": nchunks,
-                   "n_streams": w.n_streams, "staging_threads": 4,
-                   "ranges": [[r.dm_start, r.dm_step, r.n_trials, r.decimation] for r in w.ranges],
-                   "input": "pageable host memory, two 4.3 GB chunks reused",
-                   "h2d_bytes_per_step": nchunks * L * w.nchans},
-        "real_time_factor": head["real_time_factor"],
-        "gpu_launches": head["gpu_launches"],
-        "candidates_per_step": head["candidates_per_step"],
-        "clocks": head["clocks"],
-        "pageable_through_driver": {k: res["driver"][k] for k in ("value", "ms_per_step",
-                                                                  "real_time_factor")},
-        "pinned_host": {k: res["pinned"][k] for k in ("value", "ms_per_step", "real_time_factor")},
-    }
-    print(json.dumps(line))
-    return 0
-
-
 def transfer_workload(args):
     """The paper's transfer micro-experiment (Sec. 2, Sec. 2.1) on this machine: host-to-device
     throughput from pageable and from pinned memory, and the cost of allocating pinned memory
@@ -549,6 +499,74 @@ def transfer_workload(args):
     return 0
 
 
+def peaks_workload(args):
+    """The measured integer and shared-memory issue rates (dd_measure_peaks), three runs."""
+    import torch
+
+    import paper_2101_00941_gb300 as dd
+    torch.cuda.set_device(0)
+    dd.build()
+    runs = [dd.dd_measure_peaks(0) for _ in range(3)]
+    best = {k: max(r[k] for r in runs) for k in runs[0] if k != "sms"}
+    best["sms"] = runs[0]["sms"]
+    line = {"metric": "integer lane-instructions per SM-clock (LOP3 + DP2A)",
+            "value": best["int_lanes_per_clk"], "unit": "lanes/clk/SM", "n_gpus": 1,
+            "higher_is_better": True, "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": "peaks"}, "runs": runs, "best": best}
+    print(json.dumps(line))
+    return 0
+
+
+def outputs_of_chunks(w, O: int, T0: int, sizes) -> int:
+    """DM-trial*samples the library produces for chunks of `sizes` samples delivered from stream
+    position T0 on: range r outputs the decimated indices j with j*d_r in [T - O, T + n - O)."""
+    out, T = 0, T0
+    for n in sizes:
+        lo, hi = max(0, T - O), max(0, T + n - O)
+        out += sum(r.n_trials * (hi // r.decimation - lo // r.decimation) for r in w.ranges)
+        T += n
+    return out
+
+
+def launch_model(plan, w, O: int, T0: int, sizes):
+    """Summed dd_plan_model of the dedispersion launches of these chunks, in total and per range:
+    {adds, dram_bytes, smem_wavefronts, copy_bytes, outputs, launches}."""
+    keys = ("adds", "dram_bytes", "smem_wavefronts", "copy_bytes", "outputs")
+    tot = {k: 0.0 for k in keys + ("launches",)}
+    per = [dict(tot) for _ in w.ranges]
+    T = T0
+    for n in sizes:
+        lo, hi = max(0, T - O), max(0, T + n - O)
+        for r, rg in enumerate(w.ranges):
+            nout = hi // rg.decimation - lo // rg.decimation
+            if nout <= 0:
+                continue
+            m = plan.model(r, nout)
+            for k in keys:
+                per[r][k] += m[k]
+                tot[k] += m[k]
+            per[r]["launches"] += 1
+            tot["launches"] += 1
+        T += n
+    return tot, per
+
+
+def dram_traffic_per_output(w):
+    """DRAM bytes per output sample of the dedispersion launches from the committed capture, or
+    None when the capture was taken on another workload or another revision of the kernel."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+        with open(DEDISP_SOURCE, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha256") != sha:
+        return None
+    ent = rec.get("workloads", {}).get(w.name.rsplit("_", 1)[0])
+    return None if ent is None else float(ent["dram_bytes"]) / float(ent["outputs"])
+
+
 def main(args):
     import torch
 
@@ -569,39 +587,63 @@ def main(args):
             pass
     dev = torch.cuda.current_device()
     dd.build()
-    w = configs.mid(beam=rank, nsamp=args.nsamp, n_streams=args.streams)
-    xh = make_input(w, pinned=True)
-    xd = xh.cuda()
+    w, nring = stream_workload(args.workload, args.nsamp, beam=rank, streams=args.streams)
     L = w.chunk_len
     nchunks = w.nsamp // L
-    dchunks = [xd[L * k:L * (k + 1)] for k in range(nchunks)]
-    hchunks = [xh[L * k:L * (k + 1)] for k in range(nchunks)]
+    # the input ring: nring distinct seeded chunks in pinned host memory, and a copy in HBM
+    xh = torch.empty((nring, L, w.nchans), dtype=torch.uint8, pin_memory=True)
+    off = pulse_offsets(w)
+    for k in range(nring):
+        w.generate(off, t0=k * L, nsamp=L, out=xh[k].numpy())
+    xd = xh.cuda()
+    dchunks = [xd[k % nring] for k in range(nchunks)]
+    hchunks = [xh[k % nring] for k in range(nchunks)]
     plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=w.n_streams,
                    max_width=max(w.widths), peak_block=32, device=dev, flags=dd.DD_FLAG_TIMING)
     O = plan.O
-    outs = outputs_per_pass(w, O)
+    peaks = dd.dd_measure_peaks(dev)
     with ClockSampler(dev) as clk:
         ms, ncand, launches, dd_ms, dd_n = time_steps(plan, dchunks, w, args.steps, args.warmup,
                                                       barrier)
+    range_ms = [plan.stats_range(r) for r in range(len(w.ranges))]
+    T0 = args.warmup * w.nsamp  # stream position of the timed steps
+    sizes = [L] * nchunks * args.steps
+    outs = outputs_of_chunks(w, O, T0, sizes)
+    tot, per = launch_model(plan, w, O, T0, sizes)
     lat = []
     ms_e2e, ncand_e2e, _, _, _ = time_steps(plan, hchunks, w, args.steps, args.warmup, barrier,
                                             lat)
     plan.close()
     if world > 1:
         ms, ms_e2e = rank_max([ms, ms_e2e], "cuda")
-    total_outs = outs * args.steps * world
+    total_outs = outs * world
     value = total_outs / (ms * 1e-3)
     e2e = total_outs / (ms_e2e * 1e-3)
-    adds_per_launch = adds_per_pass(w, O) * args.steps / max(dd_n, 1)
-    achieved = adds_per_launch / (dd_ms * 1e-3 / max(dd_n, 1)) if dd_ms > 0 else None
-    # DRAM traffic per launch, averaged like `achieved`: the captured per-chunk bytes scaled by
-    # the step's summed chunk windows (N - O samples); only for the captured configuration
-    traffic = None
-    if (w.nchans, L, tuple(w.ranges)) == (4096, 1 << 17, tuple(configs.MID_RANGES)) and dd_n:
-        traffic = (DEDISP_DRAM_BYTES_PER_FULL_CHUNK * (w.nsamp - O) / L * args.steps / dd_n)
+    clocks = clk.summary()
+    sm_hz = (clocks["sm_mhz"] or peaks["sm_mhz"]) * 1e6
+    peak_int = peaks["int_lanes_per_clk"] * peaks["sms"] * sm_hz
+    peak_wf = peaks["lds_wavefronts_per_clk"] * peaks["sms"] * sm_hz
+    dd_s = dd_ms * 1e-3
+    achieved = tot["adds"] / dd_s if dd_s > 0 else None
+    smem_wf = tot["smem_wavefronts"] + tot["copy_bytes"] / 128.0
+    bpo = dram_traffic_per_output(w)
+    per_range = []
+    for r, (rms, rn) in enumerate(range_ms):
+        p = per[r]
+        rs = rms * 1e-3
+        per_range.append({
+            "decimation": w.ranges[r].decimation, "launches": rn, "ms": rms,
+            "adds_per_s": p["adds"] / rs if rs > 0 else None,
+            "frac": p["adds"] / rs / peak_int if rs > 0 else None,
+            "frac_smem": (p["smem_wavefronts"] + p["copy_bytes"] / 128.0) / rs / peak_wf
+            if rs > 0 and p["smem_wavefronts"] > 0 else None,
+            "dram_gbs_algorithmic": p["dram_bytes"] / rs / 1e9 if rs > 0 else None})
     obs = w.nsamp * w.tsamp
     if rank != 0:
         return 0
+    ring_note = (f"ring of {nring} distinct seeded {L}-sample chunks "
+                 f"({L * w.nchans / 1e9:.1f} GB each) reused cyclically to make up the "
+                 f"{w.nsamp}-sample beam; resident in HBM for value, pinned host memory for e2e")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -611,10 +653,11 @@ def main(args):
                    "ranges": [[r.dm_start, r.dm_step, r.n_trials, r.decimation] for r in w.ranges],
                    "chunk_len": L, "chunks": nchunks, "n_streams": w.n_streams,
                    "widths": list(w.widths), "threshold": w.threshold, "overlap": O,
-                   "l2": f"input {w.nsamp * w.nchans / 1e9:.1f} GB per step > L2 (no flush)"},
+                   "input": ring_note,
+                   "l2": f"every chunk {L * w.nchans / 1e9:.1f} GB > L2 (no flush)"},
         "real_time_factor": obs / (ms * 1e-3 / args.steps),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": w.nsamp * w.nchans,
-                "d2h_bytes_per_step": int(ncand_e2e / args.steps * 32 + nchunks * 8),
+                "d2h_bytes_per_step": int(ncand_e2e / args.steps * 32 + nchunks * 16),
                 "real_time_factor": obs / (ms_e2e * 1e-3 / args.steps),
                 # host-to-device time the streams did not hide: e2e step minus resident step
                 "exposed_copy_ms_per_chunk": max(0.0, (ms_e2e - ms) / args.steps / nchunks),
@@ -622,15 +665,30 @@ def main(args):
                                      "p99": 1e3 * float(np.percentile(lat, 99))}},
         "gpu_launches": launches,
         "candidates_per_step": ncand / args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_ADDS, "unit": "adds/s",
-                     "frac": (achieved / ALU_PEAK_ADDS) if achieved else None,
-                     "traffic": traffic, "traffic_unit": "bytes per launch",
-                     "kernel": "dedispersion", "launches_timed": dd_n,
-                     "peak_note": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)"},
-        "clocks": clk.summary(),
+        "roofline": {
+            "bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "adds/s",
+            "frac": achieved / peak_int if achieved else None,
+            "traffic": bpo * tot["outputs"] / dd_n if (bpo and dd_n) else None,
+            "traffic_unit": "bytes per launch", "kernel": "k_dedisp_tiled (all ranges)",
+            "launches_timed": dd_n, "dedisp_ms": dd_ms,
+            "peak_note": "measured: integer lane-instructions per SM-clock with LOP3 and DP2A "
+                         "interleaved (dd_measure_peaks) x SMs x median SM clock of the timed "
+                         "region; achieved counts algorithmic channel-adds (one per channel per "
+                         "output), which packed lanes let one instruction carry several of",
+            "frac_smem": smem_wf / dd_s / peak_wf if dd_s > 0 else None,
+            "smem_note": "dd_plan_model's shared-memory wavefronts (+ copy bytes / 128) of the "
+                         "timed launches over their union time, against measured conflict-free "
+                         "32-bit load wavefronts per SM-clock x SMs x clock",
+            "per_range": per_range,
+            "measured_peaks": peaks},
+        "clocks": clocks,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, xh.numpy(), O)
+        t_in0, n = baseline_window(w, O)
+        x0 = xh[0].numpy()
+        x1 = xh[1 % nring].numpy()
+        xw = np.concatenate([x0[t_in0:], x1[:n - (L - t_in0)]])
+        line["cpu_baseline"] = cpu_baseline(w, xw, t_in0, O)
     print(json.dumps(line))
     return 0
 
@@ -638,17 +696,17 @@ def main(args):
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2 for the out-of-core beam, 5 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nsamp", type=int, default=1 << 20,
-                    help="samples per beam (a multiple of 2^17; smaller only for profiler captures)")
+    ap.add_argument("--nsamp", type=int, default=None,
+                    help="samples per beam (a multiple of the chunk length; smaller only for "
+                         "tests and profiler captures)")
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the chunks rotate over")
-    ap.add_argument("--workload", choices=["mid", "serve", "batch", "ooc", "transfer"],
-                    default="mid")
-    ap.add_argument("--ooc-chunks", type=int, default=6,
-                    help="ooc: 2^19-sample chunks per step")
+    ap.add_argument("--workload", choices=["ooc", "mid", "serve", "batch", "transfer", "peaks"],
+                    default="ooc")
     ap.add_argument("--batch-scale", type=int, default=1,
                     help="batch: divide every beam's length by this (profiling only)")
     ap.add_argument("--beams", type=int, default=16, help="serve: beams")
@@ -657,12 +715,14 @@ if __name__ == "__main__":
                     help="serve: arrival rate relative to real time (1 = 4.19 s cadence)")
     ap.add_argument("--inflight", type=int, default=8, help="serve: chunks on the GPU at once")
     a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 2 if a.workload == "ooc" else 5
     if a.impl == "reference":
         sys.exit(main_reference(a))
     if a.workload == "serve":
         sys.exit(serve_workload(a))
-    if a.workload == "ooc":
-        sys.exit(ooc_workload(a))
     if a.workload == "transfer":
         sys.exit(transfer_workload(a))
+    if a.workload == "peaks":
+        sys.exit(peaks_workload(a))
     sys.exit(batch_workload(a) if a.workload == "batch" else main(a))

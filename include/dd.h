@@ -132,6 +132,33 @@ int dd_plan_info(dd_plan_t plan, int64_t* overlap, int32_t* ntrials, const int32
 int dd_plan_kernel(dd_plan_t plan, int32_t range, int32_t* kind, int32_t* tile_samples);
 
 /*
+ * dd_plan_model -- the work of one dedispersion launch of range `range` over a window of `nout`
+ * outputs, counted on the host (no GPU work); it is what roofline fractions divide by.
+ *   kind, tile_samples : as dd_plan_kernel
+ *   outputs            : DM-trial*samples, n_trials * nout
+ *   adds               : algorithmic channel-adds of the brute-force sum (Sec. 2.1), outputs*nchans
+ *   dram_bytes         : algorithmic DRAM bytes: each channel's window of decimated input
+ *                        (nout + the range's largest delay samples) read once, the int32 series
+ *                        written once
+ *   smem_wavefronts    : tiled kernel only (else 0): warp-wide shared-memory accesses the launch
+ *                        issues (one wavefront each: the kernel's accesses have no bank
+ *                        conflicts), counted from the plan-time tables
+ *   copy_bytes         : tiled kernel only: bytes its tensor and bulk copies write into shared
+ *                        memory
+ * Errors: DD_ERR_ARG.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t tile_samples;
+  int64_t outputs;
+  double adds;
+  double dram_bytes;
+  double smem_wavefronts;
+  double copy_bytes;
+} dd_launch_model_t;
+int dd_plan_model(dd_plan_t plan, int32_t range, int64_t nout, dd_launch_model_t* out);
+
+/*
  * dd_run -- enqueue the dedispersion of the next time chunk (Sec. 1, Sec. 2.1).
  *   chunk       : time-major uint8 [nsamp][nchans]; a host pointer (pinned memory gives
  *                 asynchronous copies, Sec. 2.1) or a device pointer. Read-only; it must stay
@@ -160,6 +187,28 @@ int dd_run(dd_plan_t plan, const uint8_t* chunk, int64_t nsamp, void* cuda_strea
  */
 int dd_series(dd_plan_t plan, int32_t range, const int32_t** dev_ptr, int64_t* len,
               int64_t* stride, int64_t* j0);
+
+/* Exact moments of one dedispersed series over its chunk window (Sec. 2.2: the statistics that
+ * normalise the single pulse search): s1 = sum y, s2 = sum y^2 as an unsigned 128-bit value
+ * (s2hi * 2^64 + s2lo). 32 bytes per record. */
+typedef struct {
+  int64_t s1;
+  uint64_t s2lo;
+  uint64_t s2hi;
+  uint64_t pad;
+} dd_moments_t;
+
+/*
+ * dd_moments -- device view of the most recent chunk's moments of one range (Sec. 2.2).
+ *   dev_ptr : receives a plan-owned DEVICE pointer to dd_moments_t [n_trials_r], trial order
+ *   n       : samples of the chunk window the moments cover (0: an empty window, for which the
+ *             records are not written and must not be read)
+ * The moments are accumulated by the dedispersion kernels with exact integer arithmetic and are
+ * complete once the chunk's stream has finished (dd_sync or dd_candidates); they stay valid
+ * until the chunk's slot is reused n_streams chunks later.
+ * Errors: DD_ERR_ARG (NULL plan, bad range), DD_ERR_STATE (no chunk has been run).
+ */
+int dd_moments(dd_plan_t plan, int32_t range, const dd_moments_t** dev_ptr, int64_t* n);
 
 /*
  * sps_run -- enqueue the single pulse search of the most recent chunk (Sec. 2.2).
@@ -205,6 +254,13 @@ int dd_stats(dd_plan_t plan, int64_t* launches, double* dedisp_ms, int64_t* dedi
              int32_t reset);
 
 /*
+ * dd_stats_range -- the dedispersion timing of dd_stats restricted to the launches of one range:
+ * the union of their intervals (ms) and their number, since creation or the last reset of
+ * dd_stats. Needs DD_FLAG_TIMING; complete after dd_sync. Errors: DD_ERR_ARG, DD_ERR_CUDA.
+ */
+int dd_stats_range(dd_plan_t plan, int32_t range, double* dedisp_ms, int64_t* dedisp_launches);
+
+/*
  * dd_sps_static -- the single pulse search of dd_candidates, on caller-provided device series,
  * with no memory allocated by the library. The paper has no counterpart: this entry point exists
  * for callers that cannot let a library allocate device memory at run time -- a real-time
@@ -223,14 +279,15 @@ int dd_stats(dd_plan_t plan, int64_t* launches, double* dedisp_ms, int64_t* dedi
  *   cuda_stream: cudaStream_t the work is enqueued on (NULL = the default stream); returns
  *                without waiting
  * Scratch: per-trial moments in a fixed device array of 16384 records (512 KB), which every GPU
- * that loads the library holds until the process exits. The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) with the device current, so make the
- * first call on each device before any stream capture. Every call shares the array and leaves
- * its contents behind: calls whose work may overlap on the GPU (different streams, or several
- * host threads) race on it and must be serialised by the caller. The count is cleared by the
- * call; the moments are recomputed in full.
+ * that loads the library holds until the process exits. The first call in each CUDA context
+ * looks up that array's device address (cudaGetSymbolAddress) with the device current and keeps
+ * it for that context, so make the first call on each device (and again after a context has
+ * been destroyed and re-created, e.g. by cudaDeviceReset) before any stream capture. Every call
+ * shares the array and leaves its contents behind: calls whose work may overlap on the GPU
+ * (different streams, or several host threads) race on it and must be serialised by the
+ * caller. The count is cleared by the call; the moments are recomputed in full.
  * Errors (dd_last_error explains): DD_ERR_ARG (NULL pointer, sizes outside the limits above,
- * bad widths), DD_ERR_CUDA (no device or a failed launch).
+ * bad widths, a threshold that is not finite), DD_ERR_CUDA (no device or a failed launch).
  */
 int dd_sps_static(const int32_t* series, int32_t n_trials, int64_t n, int64_t stride,
                   int32_t range, int32_t decimation, int64_t j0, const int32_t* widths,
@@ -267,9 +324,14 @@ int dd_serve_create(int32_t max_inflight, int64_t hbm_budget_bytes, int32_t devi
                     dd_server_t* out);
 
 /* dd_serve_add_beam -- plan a beam (arguments as in dd_plan; opts->device is ignored, the
- * server's device is used) and its search (widths, threshold as in sps_run). *beam receives its
- * index. Errors: those of dd_plan; DD_ERR_NOMEM when the plan would exceed the HBM budget
- * (the plan is released again). */
+ * server's device is used) and its search (widths, threshold as in sps_run, checked here so
+ * that a chunk's search cannot be refused after its dedispersion was enqueued). *beam receives
+ * its index. Errors: those of dd_plan; DD_ERR_ARG for widths outside 1..opts->max_width, not
+ * strictly increasing or more than 16 of them, or a threshold that is not finite;
+ * DD_ERR_NOMEM when the plan would exceed the HBM budget (the plan is released again).
+ * Should enqueueing a chunk of a beam still fail (a CUDA error), the beam's plan is drained and
+ * the beam is marked failed: that chunk, its chunks then on the GPU and every later chunk of
+ * the beam are reported with the error as their status. */
 int dd_serve_add_beam(dd_server_t server, const double* freqs_mhz, int32_t nchans,
                       double tsamp_s, const dd_range_t* ranges, int32_t nranges,
                       const dd_opts_t* opts, const int32_t* widths, int32_t nwidths,
@@ -379,6 +441,34 @@ int dd_tiled_plan_check(const int32_t* shifts, int32_t n_trials, int32_t cpad,
  * Errors: DD_ERR_ARG (NULL timed_out), DD_ERR_NOMEM, DD_ERR_CUDA.
  */
 int dd_selftest_wait(int32_t device, int32_t* timed_out, double* waited_ms);
+
+/*
+ * dd_measure_peaks -- measure, on `device`, the issue rates that bound the dedispersion kernels
+ * (the denominators of their roofline; not part of the paper's method). Two CTAs of 16 warps per
+ * SM run independent dependency chains of one instruction kind; rates are per SM and per SM
+ * clock, averaged over the SMs:
+ *   alu_lanes_per_clk      : LOP3 lane-instructions (the integer ALU pipe)
+ *   dp_lanes_per_clk       : DP2A lane-instructions (the integer dot-product pipe)
+ *   int_lanes_per_clk      : LOP3 and DP2A interleaved: integer lane-instructions of both pipes
+ *   add_per_clk            : 32-bit additions of plain add chains
+ *   lds_wavefronts_per_clk : warp-wide 32-bit shared-memory loads of 32 consecutive words (one
+ *                            128-byte wavefront each)
+ *   sm_mhz                 : the SM clock during the runs (cycles over nanoseconds)
+ *   sms                    : multiprocessors
+ * Takes a few milliseconds; allocates a few bytes of device memory for the duration of the call.
+ * Errors: DD_ERR_ARG (NULL out, no such device), DD_ERR_NOMEM, DD_ERR_CUDA.
+ */
+typedef struct {
+  int32_t sms;
+  int32_t pad;
+  double sm_mhz;
+  double alu_lanes_per_clk;
+  double dp_lanes_per_clk;
+  double int_lanes_per_clk;
+  double add_per_clk;
+  double lds_wavefronts_per_clk;
+} dd_peaks_t;
+int dd_measure_peaks(int32_t device, dd_peaks_t* out);
 
 /* dd_last_error -- message of the calling thread's last error ("" if none). Library-owned. */
 const char* dd_last_error(void);

@@ -35,7 +35,8 @@ EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_selftest_wait",
            "dd_stats", "dd_sps_static", "dd_serve_create", "dd_serve_add_beam", "dd_serve_submit",
            "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_batch_create",
            "dd_batch_run", "dd_batch_wait", "dd_batch_info", "dd_batch_candidates",
-           "dd_batch_destroy", "dd_plan_destroy", "dd_last_error")
+           "dd_batch_destroy", "dd_plan_destroy", "dd_last_error", "dd_moments",
+           "dd_plan_model", "dd_measure_peaks", "dd_stats_range")
 
 
 class dd_range_t(ctypes.Structure):
@@ -48,6 +49,23 @@ class dd_opts_t(ctypes.Structure):
                 ("max_width", ctypes.c_int32), ("peak_block", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("max_cands", ctypes.c_int64),
                 ("flags", ctypes.c_uint32), ("staging_threads", ctypes.c_int32)]
+
+
+class dd_launch_model_t(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("tile_samples", ctypes.c_int32),
+                ("outputs", ctypes.c_int64), ("adds", ctypes.c_double),
+                ("dram_bytes", ctypes.c_double), ("smem_wavefronts", ctypes.c_double),
+                ("copy_bytes", ctypes.c_double)]
+
+
+class dd_peaks_t(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int32), ("pad", ctypes.c_int32), ("sm_mhz", ctypes.c_double),
+                ("alu_lanes_per_clk", ctypes.c_double), ("dp_lanes_per_clk", ctypes.c_double),
+                ("int_lanes_per_clk", ctypes.c_double), ("add_per_clk", ctypes.c_double),
+                ("lds_wavefronts_per_clk", ctypes.c_double)]
+
+
+MOMENTS_DTYPE = np.dtype([("s1", "<i8"), ("s2lo", "<u8"), ("s2hi", "<u8"), ("pad", "<u8")])
 
 
 class dd_batch_beam_t(ctypes.Structure):
@@ -95,6 +113,10 @@ def lib() -> ctypes.CDLL:
         L.dd_candidates.argtypes = [vp, i64, vp, i64, P(i64), i64]
         L.dd_sync.argtypes = [vp]
         L.dd_stats.argtypes = [vp, P(i64), P(f64), P(i64), i32]
+        L.dd_moments.argtypes = [vp, i32, P(vp), P(i64)]
+        L.dd_stats_range.argtypes = [vp, i32, P(f64), P(i64)]
+        L.dd_plan_model.argtypes = [vp, i32, i64, P(dd_launch_model_t)]
+        L.dd_measure_peaks.argtypes = [i32, P(dd_peaks_t)]
         L.dd_sps_static.argtypes = [vp, i32, i64, i64, i32, i32, i64, vp, i32, f32, i32, vp, i64,
                                     vp, vp]
         L.dd_plan_destroy.argtypes = [vp]
@@ -208,6 +230,27 @@ def dd_series(plan: int, range_idx: int):
     return p.value, n.value, st.value, j0.value
 
 
+def dd_moments(plan: int, range_idx: int):
+    """(device pointer to dd_moments_t [n_trials], window length n) of the latest chunk."""
+    p, n = ctypes.c_void_p(), ctypes.c_int64()
+    _check(lib().dd_moments(plan, int(range_idx), ctypes.byref(p), ctypes.byref(n)))
+    return p.value, n.value
+
+
+def dd_plan_model(plan: int, range_idx: int, nout: int) -> dict:
+    """Work of one dedispersion launch of a range over nout outputs (see dd.h)."""
+    m = dd_launch_model_t()
+    _check(lib().dd_plan_model(plan, int(range_idx), int(nout), ctypes.byref(m)))
+    return {f: getattr(m, f) for f, _ in dd_launch_model_t._fields_}
+
+
+def dd_measure_peaks(device: int = 0) -> dict:
+    """Measured integer and shared-memory issue rates of the device (see dd.h)."""
+    p = dd_peaks_t()
+    _check(lib().dd_measure_peaks(int(device), ctypes.byref(p)))
+    return {f: getattr(p, f) for f, _ in dd_peaks_t._fields_ if f != "pad"}
+
+
 def sps_run(plan: int, widths, threshold: float):
     w = np.ascontiguousarray(widths, dtype=np.int32)
     _check(lib().sps_run(plan, w.ctypes.data, w.size, ctypes.c_float(threshold)))
@@ -231,6 +274,13 @@ def dd_stats(plan: int, reset: bool = False):
     a, b, c = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
     _check(lib().dd_stats(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(reset)))
     return a.value, b.value, c.value
+
+
+def dd_stats_range(plan: int, range_idx: int):
+    """(dedispersion ms of one range's launches, their number) -- see dd.h."""
+    b, c = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().dd_stats_range(plan, int(range_idx), ctypes.byref(b), ctypes.byref(c)))
+    return b.value, c.value
 
 
 def dd_sps_static(series_ptr: int, n_trials: int, n: int, stride: int, range_idx: int,
@@ -282,11 +332,26 @@ class Plan:
         dd_sync(self.h)
         return device_view(ptr, (ntr, stride), "<i4")[:, :n].clone(), j0
 
+    def moments(self, range_idx):
+        """The latest chunk's moments of a range as a numpy MOMENTS_DTYPE [n_trials] copy, and
+        the window length they cover."""
+        ptr, n = dd_moments(self.h, range_idx)
+        ntr = int(self.ranges[range_idx][2])
+        dd_sync(self.h)
+        raw = device_view(ptr, (ntr, 4), "<i8").cpu().numpy()
+        return raw.copy().view(MOMENTS_DTYPE).reshape(ntr), n
+
+    def model(self, range_idx, nout):
+        return dd_plan_model(self.h, range_idx, nout)
+
     def sync(self):
         dd_sync(self.h)
 
     def stats(self, reset=False):
         return dd_stats(self.h, reset)
+
+    def stats_range(self, range_idx):
+        return dd_stats_range(self.h, range_idx)
 
     def close(self):
         if self.h:

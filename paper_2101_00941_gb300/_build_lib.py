@@ -9,7 +9,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD, "libdd.so")
-SOURCES = ("dd_api.cu", "dd_kernels.cu", "dd_dedisp.cu", "dd_static.cu", "dd_serve.cu", "dd_batch.cu")
+SOURCES = ("dd_api.cu", "dd_kernels.cu", "dd_dedisp.cu", "dd_static.cu", "dd_serve.cu", "dd_batch.cu",
+           "dd_peaks.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -169,6 +169,8 @@ struct RangeKernel {
   int zcap = 0;
   size_t smem = 0;
   uint8_t* d_tabs = nullptr;  // device copy of the delay-class tables
+  int64_t lsu_wavefronts = 0; // shared-memory work of one row of time tiles (TiledPlan)
+  int64_t copy_bytes = 0;
 };
 
 struct dd_plan_s {
@@ -202,10 +204,12 @@ struct dd_plan_s {
   // are turned into [start, end) intervals against a common reference event and merged, so that
   // launches of different chunks running at the same time on different streams count once
   std::vector<cudaEvent_t> tev;
+  std::vector<int32_t> tev_range;  // range of each recorded launch
   int64_t tev_used = 0;
   cudaEvent_t tref = nullptr;
   bool tref_set = false;
   std::vector<std::pair<double, double>> intervals;
+  std::vector<int32_t> interval_range;
   double dedisp_ms = 0;
   int64_t dedisp_launches = 0;
 };
@@ -267,6 +271,7 @@ int harvest_timing(dd_plan_s* p) {
     DD_CK(cudaEventElapsedTime(&t0, p->tref, a));
     DD_CK(cudaEventElapsedTime(&t1, p->tref, b));
     p->intervals.emplace_back(t0, t1);
+    p->interval_range.push_back(p->tev_range[k]);
     p->dedisp_launches += 1;
   }
   p->tev_used = 0;
@@ -290,7 +295,7 @@ double union_ms(std::vector<std::pair<double, double>> v) {
   return total;
 }
 
-int timing_begin(dd_plan_s* p, cudaStream_t st, int64_t* slot) {
+int timing_begin(dd_plan_s* p, cudaStream_t st, int32_t range, int64_t* slot) {
   *slot = -1;
   if (!(p->opts.flags & DD_FLAG_TIMING)) return DD_OK;
   if (!p->tref_set) {
@@ -302,6 +307,7 @@ int timing_begin(dd_plan_s* p, cudaStream_t st, int64_t* slot) {
     if (rc) return rc;
   }
   *slot = p->tev_used++;
+  p->tev_range[*slot] = range;
   DD_CK(cudaEventRecord(p->tev[2 * *slot], st));
   return DD_OK;
 }
@@ -427,6 +433,8 @@ int plan_autotune(dd_plan_s* p) {
         k.row_slot = tp.row_slot;
         k.zcap = tp.zcap;
         k.smem = tp.smem;
+        k.lsu_wavefronts = tp.lsu_wavefronts;
+        k.copy_bytes = tp.copy_bytes;
       }
       ddk::TiledArgs A;
       A.xd = (l == 0) ? (const void*)s.ring1 : (const void*)s.ringd[l];
@@ -671,6 +679,8 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
           k.row_slot = tp.row_slot;
           k.zcap = tp.zcap;
           k.smem = tp.smem;
+          k.lsu_wavefronts = tp.lsu_wavefronts;
+          k.copy_bytes = tp.copy_bytes;
           break;
         }
       }
@@ -742,6 +752,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
   if (o.staging_threads > 0) p->pool = new StagingPool(o.staging_threads);
   if (o.flags & DD_FLAG_TIMING) {
     p->tev.resize(2 * 1024);
+    p->tev_range.resize(1024);
     for (auto& e : p->tev) DD_TRYCK(cudaEventCreate(&e));
     DD_TRYCK(cudaEventCreate(&p->tref));
     p->intervals.reserve(1 << 16);
@@ -770,6 +781,31 @@ int dd_plan_kernel(dd_plan_t p, int32_t range, int32_t* kind, int32_t* tile_samp
     *kind = tiled ? DD_KERNEL_TILED
                   : ((p->opts.flags & DD_FLAG_NAIVE) ? DD_KERNEL_PER_OUTPUT : DD_KERNEL_DIRECT);
   if (tile_samples) *tile_samples = tiled ? p->rk[range].tt : 0;
+  return DD_OK;
+}
+
+int dd_plan_model(dd_plan_t p, int32_t range, int64_t nout, dd_launch_model_t* out) {
+  if (!p || !out) return fail(DD_ERR_ARG, "NULL argument");
+  if (range < 0 || range >= (int32_t)p->rk.size() || nout < 0)
+    return fail(DD_ERR_ARG, "range out of bounds or nout < 0");
+  const RangeKernel& k = p->rk[range];
+  const dd_range_t& R = p->ranges[range];
+  std::memset(out, 0, sizeof *out);
+  out->kind = k.tiled ? DD_KERNEL_TILED
+                      : ((p->opts.flags & DD_FLAG_NAIVE) ? DD_KERNEL_PER_OUTPUT : DD_KERNEL_DIRECT);
+  out->tile_samples = k.tiled ? k.tt : 0;
+  out->outputs = (int64_t)R.n_trials * nout;
+  out->adds = (double)out->outputs * p->C;
+  int64_t smax = 0;
+  for (int64_t rr = p->row0[range]; rr < p->row0[range] + R.n_trials; ++rr)
+    for (int c = 0; c < p->C; ++c) smax = std::max<int64_t>(smax, p->h_shifts[rr * p->C + c]);
+  const int es = R.decimation > 1 ? 2 : 1;
+  out->dram_bytes = nout > 0 ? (double)p->C * (double)(nout + smax) * es + 4.0 * out->outputs : 0;
+  if (k.tiled && nout > 0) {
+    const double rows = (double)((nout + k.tt - 1) / k.tt);
+    out->smem_wavefronts = rows * (double)k.lsu_wavefronts;
+    out->copy_bytes = rows * (double)k.copy_bytes;
+  }
   return DD_OK;
 }
 
@@ -845,7 +881,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
     R.is_u16 = l > 0;
     if (R.nout <= 0) continue;
     int64_t ts;
-    int rc = timing_begin(p, st, &ts);
+    int rc = timing_begin(p, st, (int32_t)r, &ts);
     if (rc) return rc;
     const RangeKernel& K = p->rk[r];
     if (K.tiled) {
@@ -905,6 +941,17 @@ int dd_series(dd_plan_t p, int32_t range, const int32_t** dev_ptr, int64_t* len,
   if (len) *len = (s.hi - s.lo) / d;
   if (stride) *stride = p->series_stride[range];
   if (j0) *j0 = s.lo / d;
+  return DD_OK;
+}
+
+int dd_moments(dd_plan_t p, int32_t range, const dd_moments_t** dev_ptr, int64_t* n) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (range < 0 || range >= (int32_t)p->ranges.size()) return fail(DD_ERR_ARG, "bad range");
+  if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
+  const Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
+  const int d = p->ranges[range].decimation;
+  if (dev_ptr) *dev_ptr = reinterpret_cast<const dd_moments_t*>(s.mom + p->row0[range]);
+  if (n) *n = (s.hi - s.lo) / d;
   return DD_OK;
 }
 
@@ -1061,9 +1108,26 @@ int dd_stats(dd_plan_t p, int64_t* launches, double* dedisp_ms, int64_t* dedisp_
   if (reset) {
     p->launches = 0;
     p->intervals.clear();
+    p->interval_range.clear();
     p->dedisp_launches = 0;
     p->tref_set = false;  // the next launch records a fresh reference
   }
+  return DD_OK;
+}
+
+int dd_stats_range(dd_plan_t p, int32_t range, double* dedisp_ms, int64_t* dedisp_launches) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (range < 0 || range >= (int32_t)p->ranges.size()) return fail(DD_ERR_ARG, "bad range");
+  DD_CK(cudaSetDevice(p->device));
+  if (p->tref_set) {
+    int rc = harvest_timing(p);
+    if (rc) return rc;
+  }
+  std::vector<std::pair<double, double>> mine;
+  for (size_t k = 0; k < p->intervals.size(); ++k)
+    if (p->interval_range[k] == range) mine.push_back(p->intervals[k]);
+  if (dedisp_launches) *dedisp_launches = (int64_t)mine.size();
+  if (dedisp_ms) *dedisp_ms = union_ms(mine);
   return DD_OK;
 }
 

@@ -634,6 +634,42 @@ int tiled_tile_samples(int is_u16, int choice) {
   return choice == 0 ? 512 : 256;
 }
 
+// Host: the shared-memory work of one row of time tiles, instruction by instruction as
+// k_dedisp_tiled issues it (one wavefront per warp-wide access: the kernel's loads and stores are
+// free of bank conflicts; a 64-bit store of 32 lanes is two wavefronts). Per (trial tile, stage):
+//   accumulation : every warp loads, for its kTPW trials and TT / 64 pair-word columns, one word
+//                  per group present (trials past the range's end load too), plus the trials'
+//                  zstart entries;
+//   build        : per 32-unit block, 2 row words for each of the 8 channels and the two plane
+//                  stores; per work range, its descriptor, class entry and addressing words;
+//   addressing   : two stores per (group, class, channel) entry, by the first 8 warps;
+//   copies       : the tensor copy of the 16 staged rows and the bulk copy of the stage table.
+static void tiled_smem_work(TiledPlan& P, int ntiles, int nstages, int ngroups, bool u16) {
+  const StageTab* tabs = reinterpret_cast<const StageTab*>(P.tabs.data());
+  const int KP = P.tt / 64;
+  const int sts_per_block = u16 ? 2 : 4;
+  int64_t lsu = 0, bytes = 0;
+  for (int ti = 0; ti < ntiles; ++ti)
+    for (int s = 0; s < nstages; ++s) {
+      const StageTab& st = tabs[(size_t)ti * nstages + s];
+      const int ng = std::min(kNG, ngroups - s * kNG);
+      lsu += (int64_t)kWarps * kTPW * KP * ng;        // accumulation words
+      lsu += (int64_t)kWarps * kTPW * ng;             // zstart entries
+      lsu += kWarps;                                  // nwork
+      for (int w = 0; w < kWarps; ++w)
+        for (int k = 0; k < st.nwork[w]; ++k) {
+          const uint32_t wk = st.work[w][k];
+          const int nb = (int)(wk >> 16);
+          lsu += 5;                                   // descriptor, zlen, zoff, addr, shift
+          lsu += (int64_t)nb * (2 * kG + sts_per_block);
+        }
+      lsu += (int64_t)(kAddrEntries / 32) * 2;        // addressing stores
+      bytes += (int64_t)kRows * P.row_slot * (u16 ? 2 : 1) + (int64_t)sizeof(StageTab);
+    }
+  P.lsu_wavefronts = lsu;
+  P.copy_bytes = bytes;
+}
+
 // Host: delay classes of every (trial tile, stage) of one range, as the kernel reads them.
 // Classes are numbered in order of their first trial; a class's zlen pair words start at a
 // multiple of 4 within the stage, groups one after another, the even plane (pair words 0, 2,
@@ -750,6 +786,7 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
     P.smem = smem_layout(u16 ? 2 : 1, 4, P.row_slot, P.zcap, nst).total;
     P.ok = P.smem <= kSmemLimit;
   }
+  if (P.ok) tiled_smem_work(P, ntiles, nstages, ngroups, u16);
   return P;
 }
 

@@ -18,6 +18,7 @@ constexpr int kMaxWidths = 16;
 struct Moments {
   unsigned long long s1, s2lo, s2hi, pad;
 };
+static_assert(sizeof(Moments) == sizeof(dd_moments_t), "dd_moments views the device records");
 
 // Per-range parameters of the delay-table kernel.
 struct ShiftRange {
@@ -92,6 +93,12 @@ struct TiledPlan {
   size_t smem = 0;
   size_t tab_bytes = 0;
   std::vector<uint8_t> tabs;
+  // Shared-memory work of one row of time tiles (every trial tile of the range, TT outputs),
+  // counted from the tables as the kernel issues it: warp-wide shared-memory instructions
+  // (wavefronts of the LSU data pipe: accumulation loads, pair-word build loads and stores,
+  // table reads, addressing stores) and the bytes the tensor and bulk copies write.
+  int64_t lsu_wavefronts = 0;
+  int64_t copy_bytes = 0;
 };
 
 int tiled_tile_samples(int is_u16, int choice);

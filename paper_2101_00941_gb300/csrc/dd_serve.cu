@@ -10,6 +10,7 @@
 // fits the server's HBM budget. Latency = submission -> candidates copied to the caller.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -40,6 +41,7 @@ struct Beam {
   float threshold = 0;
   int64_t bytes = 0;
   int64_t next_seq = 0;
+  int failed = DD_OK;  // first enqueue error; a failed beam takes no further chunks
   std::deque<Request> queue, inflight;
 };
 
@@ -123,20 +125,45 @@ void dd_server_s::run() {
       Request r = pick->queue.front();
       pick->queue.pop_front();
       r.t_admit = Clock::now();
+      if (pick->failed != DD_OK) {  // the beam's stream state was lost: refuse its chunks
+        dd_serve_result_t res{r.ticket, r.beam, pick->failed, -1, 0, 0.0, 0.0};
+        done.push_back(res);
+        done_cv.notify_all();
+        progress = true;
+        continue;
+      }
       ++inflight;  // reserved while the chunk is being enqueued
       lk.unlock();
       int rc = dd_run(pick->plan, r.chunk, r.nsamp, nullptr);
+      bool ran = false;
       if (rc == DD_OK) {
+        ran = true;
         r.seq = pick->next_seq++;
         rc = sps_run(pick->plan, pick->widths.data(), (int32_t)pick->widths.size(),
                      pick->threshold);
       }
+      if (rc != DD_OK && ran) {
+        // the chunk is on the plan's slot but unsearched: finish the beam's work so the plan's
+        // slots and this beam's bookkeeping cannot disagree later
+        ddk::plan_reset(pick->plan);
+      }
       lk.lock();
       if (rc != DD_OK) {
         --inflight;
+        if (ran) {
+          pick->failed = rc;
+          // chunks of this beam already on the GPU finished with the reset; report them too
+          for (auto& q : pick->inflight) {
+            dd_serve_result_t res{q.ticket, q.beam, rc, q.seq, 0, 0.0, 0.0};
+            done.push_back(res);
+            --inflight;
+          }
+          pick->inflight.clear();
+        }
         dd_serve_result_t res{r.ticket, r.beam, rc, -1, 0, 0.0, 0.0};
         done.push_back(res);
         done_cv.notify_all();
+        progress = true;
         continue;
       }
       pick->inflight.push_back(r);
@@ -171,8 +198,16 @@ int dd_serve_create(int32_t max_inflight, int64_t hbm_budget_bytes, int32_t devi
 int dd_serve_add_beam(dd_server_t s, const double* freqs_mhz, int32_t nchans, double tsamp_s,
                       const dd_range_t* ranges, int32_t nranges, const dd_opts_t* opts,
                       const int32_t* widths, int32_t nwidths, float threshold, int32_t* beam) {
-  if (!s || !beam || !opts || !widths || nwidths < 1)
+  if (!s || !beam || !opts || !widths || nwidths < 1 || nwidths > ddk::kMaxWidths)
     return ddk::report_error(DD_ERR_ARG, "dd_serve_add_beam: bad argument");
+  // the search parameters are checked here, as sps_run would check them, so that a beam's
+  // chunks cannot fail their search after their dedispersion was enqueued
+  for (int k = 0; k < nwidths; ++k)
+    if (widths[k] < 1 || widths[k] > opts->max_width || (k > 0 && widths[k] <= widths[k - 1]))
+      return ddk::report_error(DD_ERR_ARG, "dd_serve_add_beam: widths must be strictly "
+                                           "increasing within 1..max_width");
+  if (!std::isfinite(threshold))
+    return ddk::report_error(DD_ERR_ARG, "dd_serve_add_beam: threshold must be finite");
   if (cudaSetDevice(s->device) != cudaSuccess)
     return ddk::report_error(DD_ERR_CUDA, "dd_serve_add_beam: cudaSetDevice failed");
   dd_opts_t o = *opts;

@@ -6,6 +6,9 @@
 // implicit device synchronisation of cudaMalloc/cudaFree in its processing loop, or a plug-in
 // whose host framework owns every device allocation. This entry point serves them: it
 // allocates nothing, and the caller passes the inputs and the outputs.
+#include <cudaTypedefs.h>
+
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -19,28 +22,63 @@ constexpr int32_t kStaticMaxTrials = 16384;
 // GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) ddk::Moments g_static_moments[kStaticMaxTrials];
 
-constexpr int kMaxDevices = 64;
-ddk::Moments* g_scratch_ptr[kMaxDevices] = {};
+// Device address of the scratch array, cached per CUDA context: a context that is destroyed
+// and created again (cudaDeviceReset, or a primary context released by its last user) may load
+// the module at another address, so the cache is keyed by the context handle, not the ordinal.
+constexpr int kMaxContexts = 64;
+struct ScratchEntry {
+  CUcontext ctx;
+  ddk::Moments* ptr;
+};
+ScratchEntry g_scratch[kMaxContexts] = {};
+int g_nscratch = 0;
 std::mutex g_scratch_mu;
 
 // errors go to the library's per-thread message (dd_last_error)
 int static_fail(int code, const char* msg) { return ddk::report_error(code, msg); }
 
-// Device address of the scratch array on the current device, looked up once per device (in
-// host code the array's name is only a host-side stand-in, not a device address).
-int scratch_for_current_device(ddk::Moments** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return static_fail(DD_ERR_CUDA, "dd_sps_static: no usable current CUDA device");
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+PFN_cuCtxGetCurrent_v4000 ctx_get_current() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_moments);
-    if (e != cudaSuccess || !p)
-      return static_fail(DD_ERR_CUDA, "dd_sps_static: cudaGetSymbolAddress of the scratch failed");
-    g_scratch_ptr[dev] = static_cast<ddk::Moments*>(p);
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+  });
+  return fn;
+}
+
+// Device address of the scratch array in the current context, looked up the first time a
+// context is seen (in host code the array's name is only a host-side stand-in, not a device
+// address). cudaSetDevice makes the device's primary context current if no context is yet.
+int scratch_for_current_context(ddk::Moments** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || cudaSetDevice(dev) != cudaSuccess)
+    return static_fail(DD_ERR_CUDA, "dd_sps_static: no usable current CUDA device");
+  PFN_cuCtxGetCurrent_v4000 get = ctx_get_current();
+  CUcontext ctx = nullptr;
+  if (!get || get(&ctx) != CUDA_SUCCESS || !ctx)
+    return static_fail(DD_ERR_CUDA, "dd_sps_static: no current CUDA context");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  for (int k = 0; k < g_nscratch; ++k)
+    if (g_scratch[k].ctx == ctx) {
+      *out = g_scratch[k].ptr;
+      return DD_OK;
+    }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_moments);
+  if (e != cudaSuccess || !p)
+    return static_fail(DD_ERR_CUDA, "dd_sps_static: cudaGetSymbolAddress of the scratch failed");
+  // a full cache forgets its oldest entry (contexts come and go rarely)
+  if (g_nscratch == kMaxContexts) {
+    for (int k = 1; k < kMaxContexts; ++k) g_scratch[k - 1] = g_scratch[k];
+    --g_nscratch;
   }
-  *out = g_scratch_ptr[dev];
+  g_scratch[g_nscratch++] = {ctx, static_cast<ddk::Moments*>(p)};
+  *out = static_cast<ddk::Moments*>(p);
   return DD_OK;
 }
 
@@ -65,6 +103,8 @@ int dd_sps_static(const int32_t* series, int32_t n_trials, int64_t n, int64_t st
     return static_fail(DD_ERR_ARG, "dd_sps_static: peak_block must be a power of two <= 32");
   if (nwidths < 1 || nwidths > ddk::kMaxWidths)
     return static_fail(DD_ERR_ARG, "dd_sps_static: nwidths must be 1..16");
+  if (!std::isfinite(threshold))
+    return static_fail(DD_ERR_ARG, "dd_sps_static: threshold must be finite");
   ddk::SpsArgs a;
   memset(&a, 0, sizeof a);
   int maxw = 0;
@@ -78,7 +118,7 @@ int dd_sps_static(const int32_t* series, int32_t n_trials, int64_t n, int64_t st
     }
   }
   ddk::Moments* scratch = nullptr;
-  int rc = scratch_for_current_device(&scratch);
+  int rc = scratch_for_current_context(&scratch);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   // the caller's counter must start at zero; the moments are overwritten in full, so the

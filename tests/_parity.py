@@ -67,6 +67,15 @@ def compare_candidates(gpu: np.ndarray, ref: np.ndarray, threshold: float, block
     return len(set(g) & set(o))
 
 
+def assert_moments_equal(got, want, what=""):
+    """Device moments records (MOMENTS_DTYPE rows) against the oracle's (n, S1, S2) tuples,
+    bit for bit: S1 as int64 and S2 as the full 128-bit value."""
+    assert len(got) == len(want), what
+    for k, (g, (_, s1, s2)) in enumerate(zip(got, want)):
+        g_s2 = (int(g["s2hi"]) << 64) | int(g["s2lo"])
+        assert int(g["s1"]) == s1 and g_s2 == s2, (what, k, int(g["s1"]), s1, g_s2, s2)
+
+
 def oracle_chunk(x_tm, freqs, tsamp, ranges, widths, threshold, block, chunk_sizes, trials=None):
     return oracle.run(x_tm, freqs, tsamp, ranges, widths, threshold, block, chunk_sizes,
                       trials=trials)

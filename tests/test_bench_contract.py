@@ -23,7 +23,8 @@ def _run(args, timeout):
 
 
 def test_reference_arm_line():
-    d = _run(["--impl", "reference", "--steps", "1", "--warmup", "0"], timeout=900)
+    d = _run(["--impl", "reference", "--workload", "mid", "--steps", "1", "--warmup", "0"],
+             timeout=900)
     assert d["impl"] == "reference"
     assert d["metric"] == "DM-trial·samples/s dedispersed" and d["unit"] == "DM-trial·samples/s"
     assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
@@ -38,18 +39,23 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
+    """The default (out-of-core) workload on a 2-chunk beam: every key of the contract, a
+    roofline against the measured peaks with per-range shared-memory fractions, clocks."""
     pytest.importorskip("torch")
-    d = _run(["--steps", "3", "--warmup", "3", "--nsamp", "262144", "--no-cpu-baseline"],
-             timeout=900)
+    d = _run(["--steps", "3", "--warmup", "3", "--nsamp", str(2 << 19), "--streams", "2",
+              "--no-cpu-baseline"], timeout=1200)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
               "gpu_launches", "roofline", "clocks"):
         assert k in d, k
+    assert d["config"]["workload"] == "ooc_8192ch_1048576" and d["config"]["nchans"] == 8192
     assert d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 3 and d["gpu_launches"] > 0
-    assert d["e2e"]["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 262144 * 4096
+    assert d["e2e"]["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == (2 << 19) * 8192
+    assert "exposed_copy_ms_per_chunk" in d["e2e"] and "chunk_latency_ms" in d["e2e"]
     r = d["roofline"]
-    assert r["bound"] == "alu" and 0 < r["frac"] < 1.5 and r["peak"] > 0
-    assert r["traffic"] and r["traffic"] > 0
+    assert r["bound"] == "alu" and 0 < r["frac"] < 2 and r["peak"] > 0
+    assert 0 < r["frac_smem"] < 1.5
+    assert len(r["per_range"]) == 5 and all(p["frac_smem"] for p in r["per_range"])
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
 
 
@@ -62,18 +68,23 @@ def _bench_module():
 
 
 def test_metric_counts_the_outputs_of_the_chunk_windows():
-    """The benchmark's DM-trial·samples per step (sum over ranges of n_r * (N - O) / d_r) equals
-    the outputs of the step's eight chunk windows as the oracle lays them out, and the adds are
-    one per channel per output."""
+    """The benchmark's DM-trial·samples (outputs_of_chunks) equal the outputs of the chunk
+    windows as the oracle lays them out, from the first sample and for a stream that continues
+    past its warm-up steps (full windows)."""
     import oracle
     from synth import configs
     bench = _bench_module()
     w = configs.mid()
     ranges = w.ranges_array()
     O = oracle.overlap(oracle.shift_tables(w.freqs(), w.tsamp, ranges), ranges)
-    sizes = [w.chunk_len] * (w.nsamp // w.chunk_len)
-    produced = sum(int(r[2]) * (hi // int(r[3]) - lo // int(r[3]))
-                   for (_, _, lo, hi) in oracle.chunk_windows(sizes, O) for r in ranges)
     assert O == 14496
-    assert bench.outputs_per_pass(w, O) == produced
-    assert bench.adds_per_pass(w, O) == produced * 4096
+    sizes = [w.chunk_len] * (w.nsamp // w.chunk_len)
+    for steps_before in (0, 3):
+        all_sizes = sizes * (steps_before + 1)
+        wins = oracle.chunk_windows(all_sizes, O)[len(sizes) * steps_before:]
+        produced = sum(int(r[2]) * (hi // int(r[3]) - lo // int(r[3]))
+                       for (_, _, lo, hi) in wins for r in ranges)
+        assert bench.outputs_of_chunks(w, O, steps_before * w.nsamp, sizes) == produced
+    # a continuing stream's step produces every range's full N / d_r outputs per trial
+    assert bench.outputs_of_chunks(w, O, 3 * w.nsamp, sizes) == \
+        sum(r.n_trials * (w.nsamp // r.decimation) for r in w.ranges)

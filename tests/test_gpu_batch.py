@@ -1,6 +1,7 @@
 """Batched execution (dd_batch_*): beams of different channel counts and lengths processed in
 one step -- directly, as a replayed CUDA graph, and with autotuned tiles -- give for every
-(beam, chunk) exactly the candidates of that beam processed alone."""
+(beam, chunk) the oracle's candidates (per block, tests/_parity.py) and exactly the candidates of
+that beam processed alone."""
 import numpy as np
 import pytest
 
@@ -9,6 +10,7 @@ from synth import configs
 
 torch = pytest.importorskip("torch")
 import paper_2101_00941_gb300 as dd  # noqa: E402
+from _gpu_check import oracle_candidates_match  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -30,6 +32,10 @@ def _beams():
         x = w.generate(lambda dm, f=f, w=w: oracle.delay_samples(f, w.tsamp, dm))
         out.append((w, x))
     return out
+
+
+def _sizes(w):
+    return [min(4096, w.nsamp - k) for k in range(0, w.nsamp, 4096)]
 
 
 def _alone(w, x):
@@ -58,15 +64,19 @@ def test_batch_equals_each_beam_alone(mode):
                  w0.ranges_array(), 4096, w0.widths, w0.threshold, n_streams=2,
                  graph=mode == "graph", autotune=mode == "autotune")
     try:
+        matched = 0
         for step in range(2):  # a second step (graph replay) gives the same results
             b.run()
             b.wait()
             for i, (w, x) in enumerate(beams):
                 nchunks, outputs, tile = b.info(i)
                 assert nchunks == len(want[i])
+                got = [b.candidates(i, k) for k in range(nchunks)]
                 for k in range(nchunks):
-                    np.testing.assert_array_equal(b.candidates(i, k), want[i][k])
-        assert sum(c.size for ws in want for c in ws) > 0
+                    np.testing.assert_array_equal(got[k], want[i][k])
+                if step == 1:
+                    matched += oracle_candidates_match(w, x, _sizes(w), got)
+        assert sum(c.size for ws in want for c in ws) > 0 and matched > 0
     finally:
         b.close()
 
@@ -106,15 +116,19 @@ def test_batch_of_tiled_beams(graph):
     b = dd.Batch([(w.freqs(), w.tsamp, d) for (w, _), d in zip(beams, dev)],
                  w0.ranges_array(), 4096, w0.widths, w0.threshold, n_streams=2, graph=graph)
     try:
+        matched = 0
         for step in range(2):
             b.run()
             b.wait()
-            for i in range(len(beams)):
+            for i, (w, x) in enumerate(beams):
                 nchunks, _, tile = b.info(i)
                 assert tile > 0  # range 0 runs on the tiled kernel
                 assert nchunks == len(want[i])
+                got = [b.candidates(i, k) for k in range(nchunks)]
                 for k in range(nchunks):
-                    np.testing.assert_array_equal(b.candidates(i, k), want[i][k])
-        assert sum(c.size for ws in want for c in ws) > 0
+                    np.testing.assert_array_equal(got[k], want[i][k])
+                if step == 1:
+                    matched += oracle_candidates_match(w, x, _sizes(w), got)
+        assert sum(c.size for ws in want for c in ws) > 0 and matched > 0
     finally:
         b.close()

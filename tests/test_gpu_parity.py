@@ -1,7 +1,7 @@
 """GPU path (through the C ABI) against the CPU oracle.
 
-Dedispersed series and moments bit-exact; candidates per block with SNR within
-1e-5 relative (tests/_parity.py). Covers the tiny workload whole and chunked
+Dedispersed series and the moments the library exposes (dd_moments) bit-exact;
+candidates per block with SNR within 1e-5 relative (tests/_parity.py). Covers the tiny workload whole and chunked
 over 1 and 4 streams, multi-range decimated plans with ragged chunks and
 ragged channel counts, every input kind (device, pinned, pageable), pipelined
 streams, an empty first window, and the full-size 4096-channel workload on
@@ -12,10 +12,10 @@ import pytest
 
 import oracle
 from synth import configs
-from _parity import compare_candidates
 
 torch = pytest.importorskip("torch")
 import paper_2101_00941_gb300 as dd  # noqa: E402
+from _gpu_check import _arrivals, check, run_gpu  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -24,80 +24,6 @@ pytestmark = pytest.mark.gpu
 def _built():
     dd.build()
     dd.lib()
-
-
-def _arrivals(w):
-    f = w.freqs()
-    return lambda dm: oracle.delay_samples(f, w.tsamp, dm)
-
-
-def _as_input(part, kind):
-    if kind == "device":
-        return torch.from_numpy(part).cuda()
-    if kind == "pinned":
-        return torch.from_numpy(part).pin_memory()
-    return np.ascontiguousarray(part)  # pageable (copied by the CUDA driver or staging threads)
-
-
-def run_gpu(w, x, chunk_sizes, n_streams, kind="device", flags=0, want_series=True,
-            chunk_len=None, trials=None, block=32):
-    ranges = w.ranges_array()
-    L = chunk_len or int(-(-max(chunk_sizes) // 256) * 256)
-    staging = 4 if kind == "staged" else 0
-    plan = dd.Plan(w.freqs(), w.tsamp, ranges, L, n_streams=n_streams, max_width=max(w.widths),
-                   peak_block=block, flags=flags, staging_threads=staging)
-    out = []
-    T = 0
-    try:
-        for n in chunk_sizes:
-            buf = _as_input(x[T:T + n], kind)
-            seq = plan.run(buf, n)
-            plan.search(w.widths, w.threshold)
-            cands = plan.candidates(seq)
-            series = []
-            if want_series:
-                for r in range(len(ranges)):
-                    s, j0 = plan.series(r)
-                    s = s.cpu().numpy()
-                    if trials is not None:
-                        s = s[np.asarray(trials[r])]
-                    series.append((s, j0))
-            out.append((series, cands))
-            T += n
-        O = plan.O
-        shifts = plan.shifts
-    finally:
-        plan.close()
-    return out, O, shifts
-
-
-def check(w, x, chunk_sizes, n_streams, kind="device", trials=None, flags=0, block=32):
-    ranges = w.ranges_array()
-    gpu, O, shifts = run_gpu(w, x, chunk_sizes, n_streams, kind, trials=trials, flags=flags,
-                             block=block)
-    ref = oracle.run(x, w.freqs(), w.tsamp, ranges, w.widths, w.threshold, block, chunk_sizes,
-                     trials=trials)
-    assert O == ref["O"]
-    np.testing.assert_array_equal(shifts, np.concatenate(ref["tables"]))
-    nmatch = 0
-    for k, ((series, cands), per) in enumerate(zip(gpu, ref["chunks"])):
-        for r in range(len(ranges)):
-            s, j0 = series[r]
-            assert j0 == per[r]["J0"]
-            np.testing.assert_array_equal(s, per[r]["series"], err_msg=f"chunk {k} range {r}")
-        want = np.concatenate([per[r]["cands"] for r in range(len(ranges))])
-        got = cands
-        if trials is not None:
-            keep = np.zeros(got.size, bool)
-            for r in range(len(ranges)):
-                keep |= (got["range"] == r) & np.isin(got["trial"], trials[r])
-            got = got[keep]
-        d_of = lambda r: int(ranges[r][3])
-        J0_of = lambda r, per=per: per[r]["J0"]
-        tr_index = lambda r: {int(t): i for i, t in enumerate(per[r]["trials"])}
-        series_of = lambda r, t, per=per: per[r]["series"][tr_index(r)[t]]
-        nmatch += compare_candidates(got, want, w.threshold, block, series_of, J0_of, d_of)
-    return nmatch
 
 
 # ----------------------------------------------------------------------------- tests
@@ -323,8 +249,9 @@ def test_input_kinds_give_identical_results():
     for other in res[1:]:
         for (sa, ca), (sb, cb) in zip(res[0], other):
             np.testing.assert_array_equal(ca, cb)
-            for (a, _), (b, _) in zip(sa, sb):
+            for (a, _, ma), (b, _, mb) in zip(sa, sb):
                 np.testing.assert_array_equal(a, b)
+                np.testing.assert_array_equal(ma, mb)
 
 
 def test_pipelined_streams_match_sequential():

@@ -1,5 +1,6 @@
 """Serving loop (dd_serve_*): beams of different shapes submitted interleaved give, chunk by
-chunk, exactly the candidates each beam gives alone; admission respects the HBM budget."""
+chunk, the oracle's candidates (per block, tests/_parity.py) and exactly the candidates each beam
+gives alone; admission respects the HBM budget and refuses bad search parameters."""
 import time
 
 import numpy as np
@@ -10,6 +11,7 @@ from synth import configs
 
 torch = pytest.importorskip("torch")
 import paper_2101_00941_gb300 as dd  # noqa: E402
+from _gpu_check import oracle_candidates_match  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -70,12 +72,17 @@ def test_each_chunk_is_the_same_alone_and_in_the_mix():
                 assert r["status"] == 0
                 got[r["ticket"]] = (r, c)
         assert len(got) == len(tickets)
+        per_beam = [[None] * len(sizes) for _ in beams]
         for t, (b, k) in tickets.items():
             r, c = got[t]
             assert r["beam"] == ids[b] and r["seq"] == k
             assert r["latency_ms"] >= r["queue_ms"] >= 0.0
             np.testing.assert_array_equal(c, want[b][k])
+            per_beam[b][k] = c
         assert srv.pending() == (0, 0)
+        matched = sum(oracle_candidates_match(w, x, sizes, per_beam[b])
+                      for b, (w, x) in enumerate(beams))
+        assert matched > 0
     finally:
         srv.close()
 
@@ -88,5 +95,21 @@ def test_beam_over_budget_is_refused():
         with pytest.raises(dd.DDError) as e:
             srv.add_beam(w.freqs(), w.tsamp, w.ranges_array(), 4096, w.widths, w.threshold)
         assert e.value.code == dd.DD_ERR_NOMEM
+    finally:
+        srv.close()
+
+
+def test_beam_with_bad_search_parameters_is_refused():
+    """Widths above the plan's max_width, or a threshold that is not finite, are refused when the
+    beam is added, so that no chunk's search can fail after its dedispersion was enqueued."""
+    dd.build()
+    (w, _), = _beams()[:1]
+    srv = dd.Server(max_inflight=2, hbm_budget_bytes=40 << 30)
+    try:
+        for widths, thr, mw in (((1, 2, 64), w.threshold, 32), (w.widths, float("nan"), None)):
+            with pytest.raises(dd.DDError) as e:
+                srv.add_beam(w.freqs(), w.tsamp, w.ranges_array(), 4096, widths, thr,
+                             max_width=mw)
+            assert e.value.code == dd.DD_ERR_ARG
     finally:
         srv.close()

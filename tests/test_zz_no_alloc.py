@@ -1,4 +1,5 @@
-"""dd_sps_static: the search without library allocations, against the plan's own search.
+"""dd_sps_static: the search without library allocations, against the oracle and the plan's own
+search.
 
 Callers that cannot let a library allocate device memory at run time (a real-time pipeline
 with a fixed GPU memory budget, a plug-in whose host owns all device memory) use this entry
@@ -11,7 +12,7 @@ import pytest
 
 import oracle
 from synth import configs
-from _parity import SNR_RTOL
+from _parity import SNR_RTOL, compare_candidates
 
 torch = pytest.importorskip("torch")
 import paper_2101_00941_gb300 as dd  # noqa: E402
@@ -47,6 +48,7 @@ def test_static_search_matches_plan_search_twice():
     cands = torch.zeros(cap * dd.CAND_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     xs = torch.from_numpy(x).cuda()
+    ref = oracle.run(x[:4096 * 4], f, w.tsamp, ranges, w.widths, w.threshold, 32, [4096] * 4)
     compared = 0
     try:
         for k in (2, 3):  # two chunks with full windows, searched one after the other
@@ -71,6 +73,11 @@ def test_static_search_matches_plan_search_twice():
             np.testing.assert_array_equal(got[["trial", "range", "t_start", "width"]],
                                           want[["trial", "range", "t_start", "width"]])
             np.testing.assert_allclose(got["snr"], want["snr"], rtol=SNR_RTOL)
+            per = ref["chunks"][k]
+            assert compare_candidates(
+                got, np.concatenate([per[r]["cands"] for r in range(len(ranges))]), w.threshold,
+                32, lambda r, t, per=per: per[r]["series"][t], lambda r, per=per: per[r]["J0"],
+                lambda r: int(ranges[r][3])) > 0
             compared += 1
     finally:
         plan.close()
@@ -86,3 +93,7 @@ def test_static_search_rejects_more_trials_than_its_scratch():
         dd.dd_sps_static(series.data_ptr(), 16385, 64, 64, 0, 1, 0, [1, 2], 6.0, 32,
                          cands.data_ptr(), 64, count.data_ptr())
     assert e.value.code == dd.DD_ERR_ARG and "16384" in str(e.value)
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_sps_static(series.data_ptr(), 16, 64, 64, 0, 1, 0, [1, 2], float("nan"), 32,
+                         cands.data_ptr(), 64, count.data_ptr())
+    assert e.value.code == dd.DD_ERR_ARG and "finite" in str(e.value)
