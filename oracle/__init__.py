@@ -71,6 +71,13 @@ def _load():
             lib.or_moments.argtypes = [vp, i64, vp, vp, vp]
             lib.or_sps.restype = ctypes.c_int64
             lib.or_sps.argtypes = [vp, i32, i64, vp, i32, i32, i64, vp, i32, i32, f64, vp, i64]
+            lib.or_clipped_moments.restype = None
+            lib.or_clipped_moments.argtypes = [vp, i64, i32, f64, i32, vp, vp, vp, vp]
+            lib.or_sps_clipped.restype = ctypes.c_int64
+            lib.or_sps_clipped.argtypes = [vp, i32, i64, vp, i32, i32, i64, vp, i32, i32, f64,
+                                           f64, i32, vp, i64]
+            lib.or_fof.restype = ctypes.c_int64
+            lib.or_fof.argtypes = [vp, i64, vp, vp, f64, i64, vp]
             _lib = lib
     return _lib
 
@@ -187,6 +194,77 @@ def sps(y: np.ndarray, trial_ids, range_idx: int, d: int, J0: int, widths_dec, b
                        int(J0), w.ctypes.data, int(w.size), int(block), float(threshold),
                        out.ctypes.data, int(cap))
     return out[:min(total, cap)]
+
+
+def clipped_moments(y: np.ndarray, w: int, kappa: float = 3.0, iters: int = 3):
+    """(N, T1, T2) of the clipped boxcar series B_w of one series, T2 a Python int (exact);
+    see or_clipped_moments in dd_oracle.c."""
+    lib = _load()
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    n1 = np.zeros(1, np.int64)
+    t1 = np.zeros(1, np.int64)
+    lo = np.zeros(1, np.uint64)
+    hi = np.zeros(1, np.uint64)
+    lib.or_clipped_moments(y.ctypes.data, y.size, int(w), float(kappa), int(iters),
+                           n1.ctypes.data, t1.ctypes.data, lo.ctypes.data, hi.ctypes.data)
+    return int(n1[0]), int(t1[0]), (int(hi[0]) << 64) | int(lo[0])
+
+
+def sps_clipped(y: np.ndarray, trial_ids, range_idx: int, d: int, J0: int, widths_dec,
+                block: int, threshold: float, kappa: float = 3.0, iters: int = 3,
+                cap: int | None = None) -> np.ndarray:
+    """Candidates (CAND_DTYPE) with per-width clipped statistics; see or_sps_clipped."""
+    lib = _load()
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    ntr, n = y.shape
+    tr = np.ascontiguousarray(trial_ids, dtype=np.int32)
+    w = np.ascontiguousarray(widths_dec, dtype=np.int32)
+    if cap is None:
+        cap = max(1, ntr * ((n + block - 1) // block))
+    out = np.zeros(cap, dtype=CAND_DTYPE)
+    total = lib.or_sps_clipped(y.ctypes.data, int(ntr), int(n), tr.ctypes.data, int(range_idx),
+                               int(d), int(J0), w.ctypes.data, int(w.size), int(block),
+                               float(threshold), float(kappa), int(iters), out.ctypes.data,
+                               int(cap))
+    return out[:min(total, cap)]
+
+
+GROUP_DTYPE = np.dtype([("rep", "<i8"), ("members", "<i8"), ("dm_lo", "<f8"), ("dm_hi", "<f8"),
+                        ("t_lo", "<i8"), ("t_hi", "<i8")])
+
+
+def candidate_dm(cands: np.ndarray, ranges) -> np.ndarray:
+    """DM of each candidate: dm_start + trial * dm_step of its range (FP64, as the delay table)."""
+    start = np.array([float(r[0]) for r in ranges])
+    step = np.array([float(r[1]) for r in ranges])
+    r = cands["range"].astype(np.int64)
+    return start[r] + cands["trial"].astype(np.float64) * step[r]
+
+
+def fof(cands: np.ndarray, ranges, dm_link: float, t_link: int):
+    """Friends-of-friends groups of candidates (see or_fof): per candidate the smallest index of
+    its group, and one GROUP_DTYPE record per group, in order of that index: its
+    representative (the largest SNR; ties to the smaller index), member count, DM extent and the
+    extent [t_lo, t_hi] of its boxcars in original samples."""
+    lib = _load()
+    c = np.ascontiguousarray(cands, dtype=CAND_DTYPE)
+    start = _f64([float(r[0]) for r in ranges])
+    step = _f64([float(r[1]) for r in ranges])
+    label = np.empty(c.size, dtype=np.int64)
+    if c.size:
+        lib.or_fof(c.ctypes.data, c.size, start.ctypes.data, step.ctypes.data, float(dm_link),
+                   int(t_link), label.ctypes.data)
+    dm = candidate_dm(c, ranges)
+    groups = []
+    for g in sorted(set(label.tolist())):
+        idx = np.flatnonzero(label == g)
+        rep = int(idx[0])
+        for k in idx[1:]:
+            if c["snr"][k] > c["snr"][rep]:
+                rep = int(k)
+        groups.append((rep, idx.size, dm[idx].min(), dm[idx].max(), int(c["t_start"][idx].min()),
+                       int((c["t_start"][idx] + c["width"][idx] - 1).max())))
+    return label, np.array(groups, dtype=GROUP_DTYPE)
 
 
 def widths_for_range(widths, d: int) -> np.ndarray:

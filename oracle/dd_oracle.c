@@ -241,3 +241,196 @@ int64_t or_sps(const int32_t* y, int32_t ntr, int64_t n, const int32_t* trial_id
   free(counts);
   return total;
 }
+
+/*
+ * Clipped (robust) moments of one boxcar-filtered series (Sec. 2.2 names the SPDT estimators of
+ * the single pulse search, whose definition is not in the paper; READING: iterative
+ * kappa-sigma clipping, a standard robust estimator, applied per boxcar width).
+ *   values : B_w[j] = sum_{k=j-w+1..j} y[k] for window samples j = w-1 .. n-1 (m = n-w+1 of
+ *            them); none when m <= 0
+ *   step 0 : N, T1 = sum B, T2 = sum B^2 (exact, T2 as 128 bits) over every value
+ *   step i : (i = 1 .. iters) mu = T1 / N and sd = sqrt(N*T2 - T1^2) / N in FP64 (the 128-bit
+ *            variance numerator converted to double with correct rounding);
+ *            lo = ceil(mu - kappa*sd), hi = floor(mu + kappa*sd); N, T1, T2 recomputed over
+ *            the values with lo <= B <= hi. A step whose previous variance is 0 (or N is 0)
+ *            keeps the previous statistics; the loop stops there.
+ * Returns the final N, T1 and T2 (lo/hi words).
+ */
+void or_clipped_moments(const int32_t* y, int64_t n, int32_t w, double kappa, int32_t iters,
+                        int64_t* n_out, int64_t* t1_out, uint64_t* t2lo, uint64_t* t2hi) {
+  int64_t N = 0, T1 = 0;
+  unsigned __int128 T2 = 0;
+  const int64_t m = n - w + 1;
+  int64_t* B = NULL;
+  if (m > 0) {
+    B = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+    int64_t run = 0;
+    for (int64_t k = 0; k < w - 1; ++k) run += y[k];
+    for (int64_t j = w - 1; j < n; ++j) {
+      run += y[j];
+      if (j - w >= 0) run -= y[j - w];
+      B[j - (w - 1)] = run;
+    }
+    for (int64_t k = 0; k < m; ++k) {
+      N += 1;
+      T1 += B[k];
+      T2 += (unsigned __int128)((__int128)B[k] * (__int128)B[k]);
+    }
+  }
+  for (int32_t it = 0; it < iters && N > 0; ++it) {
+    const unsigned __int128 V = (unsigned __int128)N * T2 -
+                                (unsigned __int128)((__int128)T1 * (__int128)T1);
+    if (V == 0) break;
+    const double mu = (double)T1 / (double)N;
+    const double sd = sqrt((double)V) / (double)N;
+    const double lo = ceil(mu - kappa * sd), hi = floor(mu + kappa * sd);
+    int64_t N2 = 0, S1 = 0;
+    unsigned __int128 S2 = 0;
+    for (int64_t k = 0; k < m; ++k) {
+      const double b = (double)B[k];
+      if (b >= lo && b <= hi) {
+        N2 += 1;
+        S1 += B[k];
+        S2 += (unsigned __int128)((__int128)B[k] * (__int128)B[k]);
+      }
+    }
+    N = N2;
+    T1 = S1;
+    T2 = S2;
+  }
+  free(B);
+  *n_out = N;
+  *t1_out = T1;
+  *t2lo = (uint64_t)T2;
+  *t2hi = (uint64_t)(T2 >> 64);
+}
+
+/*
+ * Boxcar single-pulse search with per-width clipped statistics (Sec. 2.2; READINGs as in
+ * or_sps, except the noise statistic): for width w the SNR of B_w[j] is
+ *      (N_w * B_w[j] - T1_w) / sqrt(N_w * T2_w - T1_w^2)
+ * i.e. (B - mu_w) / sd_w with the clipped mean and population deviation of B_w itself
+ * (or_clipped_moments; kappa, iters). A width whose clipped variance is 0 contributes nothing.
+ * Block peaks, ties, threshold and output as in or_sps.
+ */
+int64_t or_sps_clipped(const int32_t* y, int32_t ntr, int64_t n, const int32_t* trial_ids,
+                       int32_t range, int32_t d, int64_t J0, const int32_t* widths_dec, int32_t nw,
+                       int32_t block, double threshold, double kappa, int32_t iters,
+                       or_cand_t* out, int64_t cap) {
+  if (n <= 0 || ntr <= 0) return 0;
+  or_cand_t** lists = (or_cand_t**)calloc((size_t)ntr, sizeof(or_cand_t*));
+  int64_t* counts = (int64_t*)calloc((size_t)ntr, sizeof(int64_t));
+  const int64_t nblocks = (n + block - 1) / block;
+#pragma omp parallel
+  {
+    int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t* Nw = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nw > 0 ? nw : 1));
+    int64_t* T1w = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nw > 0 ? nw : 1));
+    double* den = (double*)malloc(sizeof(double) * (size_t)(nw > 0 ? nw : 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t ii = 0; ii < ntr; ++ii) {
+      const int32_t* yi = y + (size_t)ii * n;
+      for (int32_t k = 0; k < nw; ++k) {
+        uint64_t lo, hi;
+        or_clipped_moments(yi, n, widths_dec[k], kappa, iters, &Nw[k], &T1w[k], &lo, &hi);
+        const unsigned __int128 t2 = ((unsigned __int128)hi << 64) | lo;
+        const unsigned __int128 v = (unsigned __int128)Nw[k] * t2 -
+                                    (unsigned __int128)((__int128)T1w[k] * (__int128)T1w[k]);
+        den[k] = (Nw[k] > 0 && v > 0) ? sqrt((double)v) : 0.0;
+      }
+      P[0] = 0;
+      for (int64_t j = 0; j < n; ++j) P[j + 1] = P[j] + yi[j];
+      or_cand_t* mine = NULL;
+      int64_t cnt = 0;
+      for (int64_t b0 = 0; b0 < n; b0 += block) {
+        int have = 0;
+        int64_t bj = 0;
+        int32_t bw = 0;
+        double best = 0.0;
+        const int64_t b1 = b0 + block < n ? b0 + block : n;
+        for (int64_t j = b0; j < b1; ++j) {
+          for (int32_t k = 0; k < nw; ++k) {
+            const int32_t w = widths_dec[k];
+            if (j < w - 1 || den[k] == 0.0) continue;
+            const int64_t bsum = P[j + 1] - P[j + 1 - w];
+            const int64_t num = Nw[k] * bsum - T1w[k];
+            const double snr = (double)num / den[k];
+            if (!have || snr > best) {
+              have = 1;
+              best = snr;
+              bj = j;
+              bw = w;
+            }
+          }
+        }
+        if (have && best >= threshold) {
+          if (mine == NULL) mine = (or_cand_t*)malloc(sizeof(or_cand_t) * (size_t)nblocks);
+          or_cand_t* o = mine + cnt++;
+          o->trial = trial_ids[ii];
+          o->range = range;
+          o->t_start = (J0 + bj - bw + 1) * (int64_t)d;
+          o->width = bw * d;
+          o->pad = 0;
+          o->snr = best;
+        }
+      }
+      lists[ii] = mine;
+      counts[ii] = cnt;
+    }
+    free(P);
+    free(Nw);
+    free(T1w);
+    free(den);
+  }
+  int64_t total = 0;
+  for (int32_t ii = 0; ii < ntr; ++ii) {
+    for (int64_t k = 0; k < counts[ii]; ++k) {
+      if (total < cap) out[total] = lists[ii][k];
+      ++total;
+    }
+    free(lists[ii]);
+  }
+  free(lists);
+  free(counts);
+  return total;
+}
+
+/*
+ * Friends-of-friends grouping of candidates (Sec. 2.2: the single pulse search reports
+ * candidates; READING: candidates of one pulse seen at neighbouring DM trials, times and widths
+ * are merged into one group, as a single-pulse search's candidate clustering does).
+ *   DM of a candidate : dm_start[range] + trial * dm_step[range] (FP64, as the delay table)
+ *   friends(a, b)     : |DM_a - DM_b| <= dm_link  and  their boxcars [t_start, t_start + width)
+ *                       overlap or the later one starts at most t_link samples after the
+ *                       earlier one's last sample: t_a <= t_b + w_b - 1 + t_link and
+ *                       t_b <= t_a + w_a - 1 + t_link
+ *   groups            : connected components of the friendship graph
+ * label[k] receives the smallest index of candidate k's group. Plain O(n^2) union of pairs.
+ * Returns the number of groups.
+ */
+int64_t or_fof(const or_cand_t* c, int64_t n, const double* dm_start, const double* dm_step,
+               double dm_link, int64_t t_link, int64_t* label) {
+  for (int64_t k = 0; k < n; ++k) label[k] = k;
+  /* repeated relaxation: every pair of friends takes the smaller label, until nothing moves */
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int64_t a = 0; a < n; ++a) {
+      const double dma = dm_start[c[a].range] + (double)c[a].trial * dm_step[c[a].range];
+      for (int64_t b = a + 1; b < n; ++b) {
+        const double dmb = dm_start[c[b].range] + (double)c[b].trial * dm_step[c[b].range];
+        if (fabs(dma - dmb) > dm_link) continue;
+        if (c[a].t_start > c[b].t_start + c[b].width - 1 + t_link) continue;
+        if (c[b].t_start > c[a].t_start + c[a].width - 1 + t_link) continue;
+        if (label[a] != label[b]) {
+          const int64_t m = label[a] < label[b] ? label[a] : label[b];
+          label[a] = label[b] = m;
+          changed = 1;
+        }
+      }
+    }
+  }
+  int64_t groups = 0;
+  for (int64_t k = 0; k < n; ++k) groups += label[k] == k;
+  return groups;
+}
