@@ -321,6 +321,7 @@ def serve_workload(args):
     O = dd.Plan(beams[0].freqs(), beams[0].tsamp, beams[0].ranges_array(), 1 << 17).O
     lat, done_outputs, T = [], 0, {b: 0 for b in range(nbeams)}
     torch.cuda.synchronize()
+    clk = ClockSampler(dev).__enter__()
     t0 = time.perf_counter()
     pending = 0
     for (ta, b, k, n) in arr:
@@ -338,6 +339,7 @@ def serve_workload(args):
             lat.append(r["latency_ms"])
             pending -= 1
     served_s = time.perf_counter() - t0
+    clk.__exit__()
     srv.close()
     # ---- plain per-chunk loop: one stream per beam, each chunk copied, dedispersed,
     #      searched and synchronised before the next one starts
@@ -345,6 +347,7 @@ def serve_workload(args):
                      max_width=max(w.widths)) for w in beams]
     plain_lat = []
     torch.cuda.synchronize()
+    clk_plain = ClockSampler(dev).__enter__()
     t0 = time.perf_counter()
     for (ta, b, k, n) in arr:
         while time.perf_counter() - t0 < ta:
@@ -356,6 +359,7 @@ def serve_workload(args):
         p.candidates()
         plain_lat.append(1e3 * (time.perf_counter() - t_arr))
     plain_s = time.perf_counter() - t0
+    clk_plain.__exit__()
     for p in plans:
         p.close()
     obs = sum(n for (_, _, _, n) in arr) * 64e-6
@@ -370,7 +374,9 @@ def serve_workload(args):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "plain_loop": {"value": done_outputs / plain_s, "real_time_factor": obs / plain_s,
                        "latency_ms": {"p50": float(np.percentile(plain_lat, 50)),
-                                      "p99": float(np.percentile(plain_lat, 99))}},
+                                      "p99": float(np.percentile(plain_lat, 99))},
+                       "clocks": clk_plain.summary()},
+        "clocks": clk.summary(),
     }
     print(json.dumps(line))
     return 0
@@ -713,7 +719,8 @@ if __name__ == "__main__":
     ap.add_argument("--chunks-per-beam", type=int, default=6, help="serve: chunks per beam")
     ap.add_argument("--speedup", type=float, default=8.0,
                     help="serve: arrival rate relative to real time (1 = 4.19 s cadence)")
-    ap.add_argument("--inflight", type=int, default=8, help="serve: chunks on the GPU at once")
+    ap.add_argument("--inflight", type=int, default=8,
+                    help="serve: most chunks on the GPU at once (the admission limit's cap)")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = 2 if a.workload == "ooc" else 5

@@ -294,6 +294,39 @@ int dd_sps_static(const int32_t* series, int32_t n_trials, int64_t n, int64_t st
                   int32_t nwidths, float threshold, int32_t peak_block, dd_cand_t* cands,
                   int64_t cap, unsigned long long* count, void* cuda_stream);
 
+/*
+ * dd_group_candidates -- friends-of-friends grouping of candidates (Sec. 2.2: one pulse is
+ * reported at neighbouring DM trials, times and widths; reading: a single-pulse search's
+ * candidate clustering). Host only, no GPU work.
+ *   cands, n   : host candidates, e.g. one chunk's from dd_candidates (sorted as it returns
+ *                them; any order works, indices refer to this order)
+ *   ranges     : host [nranges] the plan's DM ranges (the DM of a candidate is
+ *                dm_start + trial * dm_step of its range)
+ *   dm_link    : candidates whose DMs differ by at most this much (pc cm^-3) ...
+ *   t_link     : ... and whose boxcars [t_start, t_start + width) overlap or leave at most
+ *                t_link original samples between the earlier one's last sample and the later
+ *                one's first, are friends; groups are the connected components of friendship
+ *   out, cap   : host dd_group_t [cap]: one record per group in order of its smallest index:
+ *                rep (index of the member with the largest SNR; ties to the smaller index),
+ *                members, the DM extent and the first and last original sample of its boxcars
+ *   ngroups    : receives the number of groups
+ *   label      : host int64 [n] or NULL: receives each candidate's group as the smallest index
+ *                of its members
+ * Errors: DD_ERR_ARG (bad sizes, a candidate's range or width, non-finite or negative links),
+ * DD_ERR_CAP (more groups than cap; *ngroups holds the true count).
+ */
+typedef struct {
+  int64_t rep;
+  int64_t members;
+  double dm_lo;
+  double dm_hi;
+  int64_t t_lo;
+  int64_t t_hi;
+} dd_group_t;
+int dd_group_candidates(const dd_cand_t* cands, int64_t n, const dd_range_t* ranges,
+                        int32_t nranges, double dm_link, int64_t t_link, dd_group_t* out,
+                        int64_t cap, int64_t* ngroups, int64_t* label);
+
 /* dd_plan_destroy -- wait for the plan's work and free everything it allocated. NULL is a no-op. */
 void dd_plan_destroy(dd_plan_t plan);
 
@@ -301,10 +334,15 @@ void dd_plan_destroy(dd_plan_t plan);
  * Many beams, each with a plan of its own, whose chunks arrive at arbitrary times (Sec. 1: work
  * split over CUDA streams, applied across beams; Sec. 2.2: every buffer allocated when a beam is
  * planned). A dispatcher thread owned by the server makes every plan call: a submitted chunk
- * waits in its beam's queue and is started, in arrival order, as soon as fewer than
- * max_inflight chunks are on the GPU and its beam has a free stream slot; chunks of different
- * beams then run concurrently, each beam on its own streams, and a chunk gives the same
- * candidates as it would with its beam alone. */
+ * waits in its beam's queue and is started, oldest first across beams, as soon as fewer chunks
+ * are on the GPU than the admission limit and its beam has a free stream slot (at most
+ * n_streams chunks of one beam in flight); chunks of different beams then run concurrently,
+ * each beam on its own streams, and a chunk gives the same candidates as it would with its
+ * beam alone. Admission limit: with at most two requests waiting, two chunks may be on the GPU
+ * and the newer one's dedispersion is ordered after the older one's search (its copy, corner
+ * turn and decimation overlap it), so that chunks finish in arrival order close to their own
+ * service time; with a longer backlog, as many chunks as are waiting (at most max_inflight) run
+ * unordered, so that their launches fill each other's gaps. */
 typedef struct dd_server_s* dd_server_t;
 
 typedef struct {
@@ -318,7 +356,7 @@ typedef struct {
 } dd_serve_result_t;
 
 /* dd_serve_create -- start a server on `device` that keeps at most max_inflight chunks on the
- * GPU and accepts beams whose plans fit hbm_budget_bytes of device memory in total.
+ * GPU (the cap of the admission limit above) and accepts beams whose plans fit hbm_budget_bytes of device memory in total.
  * Errors: DD_ERR_ARG. */
 int dd_serve_create(int32_t max_inflight, int64_t hbm_budget_bytes, int32_t device,
                     dd_server_t* out);

@@ -36,7 +36,7 @@ EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_selftest_wait",
            "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_batch_create",
            "dd_batch_run", "dd_batch_wait", "dd_batch_info", "dd_batch_candidates",
            "dd_batch_destroy", "dd_plan_destroy", "dd_last_error", "dd_moments",
-           "dd_plan_model", "dd_measure_peaks", "dd_stats_range")
+           "dd_plan_model", "dd_measure_peaks", "dd_stats_range", "dd_group_candidates")
 
 
 class dd_range_t(ctypes.Structure):
@@ -64,6 +64,9 @@ class dd_peaks_t(ctypes.Structure):
                 ("int_lanes_per_clk", ctypes.c_double), ("add_per_clk", ctypes.c_double),
                 ("lds_wavefronts_per_clk", ctypes.c_double)]
 
+
+GROUP_DTYPE = np.dtype([("rep", "<i8"), ("members", "<i8"), ("dm_lo", "<f8"), ("dm_hi", "<f8"),
+                        ("t_lo", "<i8"), ("t_hi", "<i8")])
 
 MOMENTS_DTYPE = np.dtype([("s1", "<i8"), ("s2lo", "<u8"), ("s2hi", "<u8"), ("pad", "<u8")])
 
@@ -115,6 +118,7 @@ def lib() -> ctypes.CDLL:
         L.dd_stats.argtypes = [vp, P(i64), P(f64), P(i64), i32]
         L.dd_moments.argtypes = [vp, i32, P(vp), P(i64)]
         L.dd_stats_range.argtypes = [vp, i32, P(f64), P(i64)]
+        L.dd_group_candidates.argtypes = [vp, i64, vp, i32, f64, i64, vp, i64, P(i64), vp]
         L.dd_plan_model.argtypes = [vp, i32, i64, P(dd_launch_model_t)]
         L.dd_measure_peaks.argtypes = [i32, P(dd_peaks_t)]
         L.dd_sps_static.argtypes = [vp, i32, i64, i64, i32, i32, i64, vp, i32, f32, i32, vp, i64,
@@ -274,6 +278,21 @@ def dd_stats(plan: int, reset: bool = False):
     a, b, c = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
     _check(lib().dd_stats(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(reset)))
     return a.value, b.value, c.value
+
+
+def dd_group_candidates(cands: np.ndarray, ranges, dm_link: float, t_link: int):
+    """(per-candidate group label, GROUP_DTYPE records) -- friends-of-friends; see dd.h."""
+    c = np.ascontiguousarray(cands, dtype=CAND_DTYPE)
+    rr = (dd_range_t * len(ranges))(*[dd_range_t(float(r[0]), float(r[1]), int(r[2]), int(r[3]))
+                                      for r in ranges])
+    out = np.zeros(max(1, c.size), dtype=GROUP_DTYPE)
+    label = np.zeros(max(1, c.size), dtype=np.int64)
+    n = ctypes.c_int64()
+    _check(lib().dd_group_candidates(c.ctypes.data if c.size else None, c.size,
+                                     ctypes.addressof(rr), len(ranges), float(dm_link),
+                                     int(t_link), out.ctypes.data, out.size, ctypes.byref(n),
+                                     label.ctypes.data))
+    return label[:c.size], out[:n.value]
 
 
 def dd_stats_range(plan: int, range_idx: int):

@@ -10,9 +10,12 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD, "libdd.so")
 SOURCES = ("dd_api.cu", "dd_kernels.cu", "dd_dedisp.cu", "dd_static.cu", "dd_serve.cu", "dd_batch.cu",
-           "dd_peaks.cu")
+           "dd_peaks.cu", "dd_group.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code without floating-point contraction: FP64 host arithmetic (candidate DMs) rounds once
+# per operation on x86 and Arm alike
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 

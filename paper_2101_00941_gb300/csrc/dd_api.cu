@@ -200,6 +200,7 @@ struct dd_plan_s {
   int64_t launches = 0;
   StagingPool* pool = nullptr;     // staging_threads > 0
   int32_t* err_word = nullptr;     // if set, kernel error bits go here instead of the slot's
+  cudaEvent_t gate = nullptr;      // if set, the next chunk's dedispersion waits for it (once)
   // dedispersion timing (DD_FLAG_TIMING): every launch is bracketed by an event pair; the pairs
   // are turned into [start, end) intervals against a common reference event and merged, so that
   // launches of different chunks running at the same time on different streams count once
@@ -492,6 +493,15 @@ int plan_autotune(dd_plan_s* p) {
 }
 
 int range_tile(dd_plan_s* p, int r) { return p->rk[r].tiled ? p->rk[r].tt : 0; }
+
+void plan_gate_next(dd_plan_s* p, cudaEvent_t ev) { p->gate = ev; }
+
+cudaEvent_t chunk_done_event(dd_plan_s* p, int64_t seq) {
+  const int64_t S = (int64_t)p->slots.size();
+  if (seq < 0 || seq >= p->next_seq || seq < p->next_seq - S) return nullptr;
+  Slot& s = p->slots[seq % S];
+  return (s.seq == seq && s.searched) ? s.ev_sps : nullptr;
+}
 
 void plan_redirect_errors(dd_plan_s* p, int32_t* err) { p->err_word = err; }
 
@@ -861,6 +871,12 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
     DD_CK(ddk::launch_decimate(in, l > 1, in_stride, s.ringd[l], p->Rd[l], p->Cp,
                                (H + nsamp) >> l, st));
     p->launches += 1;
+  }
+  // an external ordering point (serving: another beam's chunk must finish first); the copy,
+  // corner turn and decimation above still overlap that chunk's work
+  if (p->gate) {
+    DD_CK(cudaStreamWaitEvent(st, p->gate, 0));
+    p->gate = nullptr;
   }
   const int64_t T = p->T_total;
   const int64_t lo = std::max<int64_t>(0, T - p->O), hi = std::max<int64_t>(0, T + nsamp - p->O);

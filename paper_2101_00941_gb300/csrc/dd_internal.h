@@ -138,6 +138,11 @@ int sps_enqueue(dd_plan_s* plan, const int32_t* widths, int32_t nwidths, float t
 int plan_autotune(dd_plan_s* plan);
 int range_tile(dd_plan_s* plan, int r);
 void plan_redirect_errors(dd_plan_s* plan, int32_t* err);
+// Serving support: make the next dd_run's dedispersion wait (once) for an event of another
+// plan on the same device; the event recorded when chunk `seq` of a plan has been searched
+// (nullptr if that chunk is not a searched chunk still held by the plan).
+void plan_gate_next(dd_plan_s* plan, cudaEvent_t ev);
+cudaEvent_t chunk_done_event(dd_plan_s* plan, int64_t seq);
 
 // ---- launchers (dd_kernels.cu); each returns the cudaGetLastError() of its launch
 cudaError_t launch_shift_table(const double* freqs, int32_t nchans, int32_t cpad, double fref,

@@ -1,13 +1,23 @@
 // Serving loop: many beams, each a plan of its own, whose chunks arrive at arbitrary times.
 //
 // A dispatcher thread owns every plan call. Requests wait in per-beam FIFO queues and are
-// admitted in arrival order as soon as (a) fewer than max_inflight chunks are on the GPU and
-// (b) the request's beam has a free stream slot (its plan keeps n_streams chunks in flight).
-// So a chunk that arrives while others are being processed starts as soon as capacity frees
-// up, and chunks of different beams overlap on the device, each beam on its own streams (Sec.
-// 1: work split over CUDA streams; Sec. 2.2: all memory allocated when a beam is planned, so
-// admitting a chunk allocates nothing). A beam is accepted only if its plan's device memory
-// fits the server's HBM budget. Latency = submission -> candidates copied to the caller.
+// admitted oldest first across beams as soon as (a) fewer chunks are on the GPU than the
+// admission limit below and (b) the request's beam has a free stream slot (its plan keeps
+// n_streams chunks in flight: the per-beam cap). So a chunk that arrives while others are
+// being processed starts as soon as capacity frees up, and chunks of different beams overlap on
+// the device, each beam on its own streams (Sec. 1: work split over CUDA streams; Sec. 2.2: all
+// memory allocated when a beam is planned, so admitting a chunk allocates nothing). A beam is
+// accepted only if its plan's device memory fits the server's HBM budget. Latency = submission
+// -> candidates copied to the caller.
+//
+// Admission limit. One chunk's dedispersion launches already fill the GPU (thousands of CTAs),
+// so chunks sharing the GPU mostly slow each other down; overlap pays only in the gaps between
+// launches and at their partial last waves. The limit therefore follows the backlog: with at
+// most two requests waiting, two chunks may be on the GPU, and the newer one's dedispersion is
+// ordered after the older one's search (its copy, corner turn and decimation still overlap
+// it), so chunks complete in arrival order at close to their own service time; with a longer
+// backlog, up to as many chunks as are waiting (never more than max_inflight) run unordered, so
+// that their launches fill each other's gaps and throughput rises.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -64,6 +74,8 @@ struct dd_server_s {
   bool stop = false;
   int inflight = 0;
   int64_t next_ticket = 0;
+  dd_plan_t last_plan = nullptr;  // the most recently admitted chunk
+  int64_t last_seq = -1;
 
   void run();
 };
@@ -114,8 +126,15 @@ void dd_server_s::run() {
       done_cv.notify_all();
       progress = true;
     }
-    // admissions: earliest submitted request whose beam has a free slot
-    while (!stop && inflight < max_inflight) {
+    // admissions: earliest submitted request whose beam has a free slot, while fewer chunks
+    // are on the GPU than the backlog-dependent limit
+    for (;;) {
+      if (stop) break;
+      int64_t queued = 0;
+      for (auto* bm : beams) queued += (int64_t)bm->queue.size();
+      const int limit = (int)std::min<int64_t>(max_inflight, std::max<int64_t>(2, queued));
+      if (inflight >= limit) break;
+      const bool ordered = queued <= 2;  // light load: complete in arrival order
       Beam* pick = nullptr;
       for (auto* bm : beams) {
         if (bm->queue.empty() || (int)bm->inflight.size() >= bm->n_streams) continue;
@@ -133,7 +152,13 @@ void dd_server_s::run() {
         continue;
       }
       ++inflight;  // reserved while the chunk is being enqueued
+      dd_plan_t prev_plan = last_plan;
+      const int64_t prev_seq = last_seq;
       lk.unlock();
+      if (ordered && prev_plan && inflight > 1) {
+        cudaEvent_t ev = ddk::chunk_done_event(prev_plan, prev_seq);
+        if (ev) ddk::plan_gate_next(pick->plan, ev);
+      }
       int rc = dd_run(pick->plan, r.chunk, r.nsamp, nullptr);
       bool ran = false;
       if (rc == DD_OK) {
@@ -167,6 +192,8 @@ void dd_server_s::run() {
         continue;
       }
       pick->inflight.push_back(r);
+      last_plan = pick->plan;
+      last_seq = r.seq;
       progress = true;
     }
     if (!progress) work_cv.wait_for(lk, std::chrono::microseconds(inflight ? 50 : 2000));
