@@ -50,8 +50,15 @@ extern "C" {
 #define DD_FLAG_NAIVE 2u    /* use the one-thread-per-output dedispersion kernel (testing aid) */
 #define DD_FLAG_DEVICE_INPUT 4u /* chunks are always in device memory: no staging buffer is
                                    allocated and host chunks are refused (DD_ERR_ARG) */
-#define DD_FLAG_TILE256 8u  /* plan the tiled kernel with 256-sample time tiles first (testing
+#define DD_FLAG_TILE256 8u  /* plan the tiled kernel with 256-sample time tiles only (testing
                                aid; 512-sample tiles are tried first otherwise) */
+#define DD_FLAG_TRIALS32 16u /* plan the tiled kernel with 32-trial tiles only (testing aid;
+                                64-trial tiles are tried first otherwise) */
+#define DD_FLAG_AUTOTUNE 32u /* dd_plan times every tile shape that fits each range (trials x
+                                outputs x threads: 64 x 512 x 512, 64 x 512 x 1024, 64 x 256 x
+                                512, 32 x 256 x 512) on the plan's own buffers and keeps the
+                                fastest (adds a few launches per range to planning) */
+#define DD_FLAG_WARPS32 64u /* plan the tiled kernel with 1024-thread CTAs only (testing aid) */
 
 typedef struct dd_plan_s* dd_plan_t;
 
@@ -119,7 +126,7 @@ int dd_plan_info(dd_plan_t plan, int64_t* overlap, int32_t* ntrials, const int32
 
 /*
  * dd_plan_kernel -- which dedispersion kernel range `range` (0-based, plan order) runs on.
- *   kind         : DD_KERNEL_TILED (delay classes shared by a 64-trial tile), DD_KERNEL_DIRECT
+ *   kind         : DD_KERNEL_TILED (delay classes shared by a trial tile), DD_KERNEL_DIRECT
  *                  (the fallback where the range's delay classes or decimation exceed the tiled
  *                  kernel's limits: coarse channels, decimation above x16) or
  *                  DD_KERNEL_PER_OUTPUT (one thread per output, with DD_FLAG_NAIVE) (may be NULL)
@@ -135,6 +142,9 @@ int dd_plan_kernel(dd_plan_t plan, int32_t range, int32_t* kind, int32_t* tile_s
  * dd_plan_model -- the work of one dedispersion launch of range `range` over a window of `nout`
  * outputs, counted on the host (no GPU work); it is what roofline fractions divide by.
  *   kind, tile_samples : as dd_plan_kernel
+ *   tile_trials        : trials per tile of the tiled kernel (64 or 32), else 0
+ *   cta_threads        : threads per CTA of the tiled kernel (512 or 1024), else 0
+ *   ctas_per_sm        : CTAs of the tiled kernel's tile shape per SM (1 or 2), else 0
  *   outputs            : DM-trial*samples, n_trials * nout
  *   adds               : algorithmic channel-adds of the brute-force sum (Sec. 2.1), outputs*nchans
  *   dram_bytes         : algorithmic DRAM bytes: each channel's window of decimated input
@@ -150,6 +160,10 @@ int dd_plan_kernel(dd_plan_t plan, int32_t range, int32_t* kind, int32_t* tile_s
 typedef struct {
   int32_t kind;
   int32_t tile_samples;
+  int32_t tile_trials;
+  int32_t cta_threads;
+  int32_t ctas_per_sm;
+  int32_t pad;
   int64_t outputs;
   double adds;
   double dram_bytes;
@@ -458,13 +472,14 @@ void dd_serve_destroy(dd_server_t server);
  *   shifts       : int32 [n_trials][cpad], delays of one range in decimated samples, channels
  *                  padded to cpad (a multiple of 8) by repeating the last channel
  *   tile_samples : 512 or 256 (outputs per time tile)
+ *   tile_trials  : 64 or 32 (trials per tile)
  *   ok           : receives 1 if the tiled kernel can run the range, else 0
  *   violations   : receives the number of violated checks (0 expected; 0 when ok is 0)
  * Errors: DD_ERR_ARG.
  */
 int dd_tiled_plan_check(const int32_t* shifts, int32_t n_trials, int32_t cpad,
-                        int32_t decimation, int32_t tile_samples, int32_t* ok,
-                        int64_t* violations);
+                        int32_t decimation, int32_t tile_samples, int32_t tile_trials,
+                        int32_t* ok, int64_t* violations);
 
 /*
  * dd_selftest_wait -- failure-detection self-test of the device-side bounded wait. The tiled

@@ -27,6 +27,9 @@ DD_FLAG_TIMING = 1
 DD_FLAG_NAIVE = 2
 DD_FLAG_DEVICE_INPUT = 4
 DD_FLAG_TILE256 = 8
+DD_FLAG_TRIALS32 = 16
+DD_FLAG_AUTOTUNE = 32
+DD_FLAG_WARPS32 = 64
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
 
@@ -53,6 +56,8 @@ class dd_opts_t(ctypes.Structure):
 
 class dd_launch_model_t(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("tile_samples", ctypes.c_int32),
+                ("tile_trials", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("outputs", ctypes.c_int64), ("adds", ctypes.c_double),
                 ("dram_bytes", ctypes.c_double), ("smem_wavefronts", ctypes.c_double),
                 ("copy_bytes", ctypes.c_double)]
@@ -109,7 +114,7 @@ def lib() -> ctypes.CDLL:
         L.dd_plan_info.argtypes = [vp, P(i64), P(i32), P(vp)]
         L.dd_plan_kernel.argtypes = [vp, i32, P(i32), P(i32)]
         L.dd_selftest_wait.argtypes = [i32, P(i32), P(ctypes.c_double)]
-        L.dd_tiled_plan_check.argtypes = [vp, i32, i32, i32, i32, P(i32), P(i64)]
+        L.dd_tiled_plan_check.argtypes = [vp, i32, i32, i32, i32, i32, P(i32), P(i64)]
         L.dd_run.argtypes = [vp, vp, i64, vp]
         L.dd_series.argtypes = [vp, i32, P(vp), P(i64), P(i64), P(i64)]
         L.sps_run.argtypes = [vp, vp, i32, f32]
@@ -211,13 +216,14 @@ def dd_selftest_wait(device: int = 0):
     return t.value, ms.value
 
 
-def dd_tiled_plan_check(shifts, decimation: int, tile_samples: int = 512):
+def dd_tiled_plan_check(shifts, decimation: int, tile_samples: int = 512, tile_trials: int = 64):
     """Host-only check of the tiled plan of one range (see dd.h): (ok, violations).
     `shifts` is int32 [n_trials][cpad] with cpad a multiple of 8."""
     a = np.ascontiguousarray(shifts, dtype=np.int32)
     ok, bad = ctypes.c_int32(), ctypes.c_int64()
     _check(lib().dd_tiled_plan_check(a.ctypes.data, a.shape[0], a.shape[1], int(decimation),
-                                     int(tile_samples), ctypes.byref(ok), ctypes.byref(bad)))
+                                     int(tile_samples), int(tile_trials), ctypes.byref(ok),
+                                     ctypes.byref(bad)))
     return ok.value, bad.value
 
 

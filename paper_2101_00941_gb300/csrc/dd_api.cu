@@ -163,6 +163,9 @@ struct Slot {
 struct RangeKernel {
   bool tiled = false;
   int tt = 0;
+  int trials = 0;             // trials per tile
+  int threads = 0;            // threads per CTA
+  int ctas = 0;               // CTAs per SM of the tile shape
   int nseg = 0;
   int nstage = 0;
   int row_slot = 0;
@@ -262,6 +265,42 @@ int dalloc(T** ptr, size_t bytes, const char* what) {
   }
   return DD_OK;
 }
+
+// Plan one range on the tiled kernel with one tile shape (tt outputs x trials trials): the
+// delay-class tables on the device and the kernel instance's shared-memory attribute. *ok =
+// false (and nothing allocated) when the shape does not fit the range.
+int plan_tiled_shape(const int32_t* tab, int ntr, int cpad, int d, int tt, int trials,
+                     int threads, RangeKernel* k, bool* ok) {
+  *ok = false;
+  ddk::TiledPlan tp = ddk::tiled_plan(tab, ntr, cpad, d, tt, trials, threads);
+  if (!tp.ok) return DD_OK;
+  RangeKernel r;
+  if (dalloc(&r.d_tabs, tp.tab_bytes, "delay-class tables")) return DD_ERR_NOMEM;
+  cudaError_t e = cudaMemcpy(r.d_tabs, tp.tabs.data(), tp.tab_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = ddk::prepare_tiled(d > 1, tt, tp.nstage, trials, threads, tp.smem);
+  if (e != cudaSuccess) {
+    cudaFree(r.d_tabs);
+    return fail(DD_ERR_CUDA, "tiled kernel set-up: %s", cudaGetErrorString(e));
+  }
+  r.tiled = true;
+  r.tt = tt;
+  r.trials = trials;
+  r.threads = threads;
+  r.ctas = tp.ctas;
+  r.nseg = tp.nseg;
+  r.nstage = tp.nstage;
+  r.row_slot = tp.row_slot;
+  r.zcap = tp.zcap;
+  r.smem = tp.smem;
+  r.lsu_wavefronts = tp.lsu_wavefronts;
+  r.copy_bytes = tp.copy_bytes;
+  *k = r;
+  *ok = true;
+  return DD_OK;
+}
+
+// Tile shapes (outputs, trials, threads per CTA) in the order a plan tries them.
+constexpr int kShapes[4][3] = {{512, 64, 512}, {512, 64, 1024}, {256, 64, 512}, {256, 32, 512}};
 
 // Turn recorded event pairs into intervals relative to the reference event.
 int harvest_timing(dd_plan_s* p) {
@@ -408,34 +447,15 @@ int plan_autotune(dd_plan_s* p) {
     }
     float best_ms = 1e30f;
     RangeKernel best = cur;
-    for (int choice = 0; choice < 2; ++choice) {
-      const int tt = ddk::tiled_tile_samples(u16, choice);
+    for (int shape = 0; shape < 4; ++shape) {
+      const int tt = kShapes[shape][0], trials = kShapes[shape][1], nt = kShapes[shape][2];
       RangeKernel k = cur;
-      ddk::TiledPlan tp;
-      if (tt == cur.tt) {
-        k = cur;
-      } else {
-        tp = ddk::tiled_plan(tab.data(), p->ranges[r].n_trials, p->Cp, d, tt);
-        if (!tp.ok) continue;
-        if (dalloc(&k.d_tabs, tp.tab_bytes, "delay-class tables")) {
-          rc = DD_ERR_NOMEM;
-          break;
-        }
-        if (cudaMemcpy(k.d_tabs, tp.tabs.data(), tp.tab_bytes, cudaMemcpyHostToDevice) !=
-                cudaSuccess ||
-            ddk::prepare_tiled(u16, tt, tp.nstage, tp.smem) != cudaSuccess) {
-          cudaFree(k.d_tabs);
-          rc = fail(DD_ERR_CUDA, "autotune: set-up failed");
-          break;
-        }
-        k.tt = tt;
-        k.nseg = tp.nseg;
-        k.nstage = tp.nstage;
-        k.row_slot = tp.row_slot;
-        k.zcap = tp.zcap;
-        k.smem = tp.smem;
-        k.lsu_wavefronts = tp.lsu_wavefronts;
-        k.copy_bytes = tp.copy_bytes;
+      if (tt != cur.tt || trials != cur.trials || nt != cur.threads) {
+        bool ok = false;
+        rc = plan_tiled_shape(tab.data(), p->ranges[r].n_trials, p->Cp, d, tt, trials, nt, &k,
+                              &ok);
+        if (rc) break;
+        if (!ok) continue;
       }
       ddk::TiledArgs A;
       A.xd = (l == 0) ? (const void*)s.ring1 : (const void*)s.ringd[l];
@@ -459,13 +479,18 @@ int plan_autotune(dd_plan_s* p) {
       A.nstage = k.nstage;
       A.tabs = k.d_tabs;
       A.err = reinterpret_cast<int32_t*>(s.d_count + 1);
-      float ms = 0;
-      cudaError_t e = ddk::launch_tiled(A, u16, k.tt, s.stream);  // warm-up
-      if (e == cudaSuccess) e = cudaEventRecord(e0, s.stream);
-      if (e == cudaSuccess) e = ddk::launch_tiled(A, u16, k.tt, s.stream);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, s.stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      // one warm-up launch, then the better of two timed ones
+      float ms = 1e30f;
+      cudaError_t e = ddk::launch_tiled(A, u16, k.tt, k.trials, k.threads, s.stream);
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        float t = 0;
+        e = cudaEventRecord(e0, s.stream);
+        if (e == cudaSuccess) e = ddk::launch_tiled(A, u16, k.tt, k.trials, k.threads, s.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
       if (e != cudaSuccess) {
         if (k.d_tabs != cur.d_tabs) cudaFree(k.d_tabs);
         rc = fail(DD_ERR_CUDA, "autotune: timing launch failed: %s", cudaGetErrorString(e));
@@ -662,36 +687,21 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     p->rk.resize(nranges);
     if (!(o.flags & DD_FLAG_NAIVE)) {
       for (int r = 0; r < nranges; ++r) {
-        const bool u16 = ranges[r].decimation > 1;
-        const int first = (o.flags & DD_FLAG_TILE256) ? 1 : 0;
-        for (int choice = first; choice < 2; ++choice) {
-          const int tt = ddk::tiled_tile_samples(u16, choice);
-          ddk::TiledPlan tp = ddk::tiled_plan(&full[(size_t)p->row0[r] * p->Cp],
-                                              ranges[r].n_trials, p->Cp,
-                                              ranges[r].decimation, tt);
-          if (!tp.ok) continue;
-          RangeKernel& k = p->rk[r];
-          if (dalloc(&k.d_tabs, tp.tab_bytes, "delay-class tables")) {
+        // the first shape that fits, in kShapes order; testing aids force the 256-output tile
+        // (DD_FLAG_TILE256) or the 32-trial tile (DD_FLAG_TRIALS32)
+        for (int shape = 0; shape < 4 && !p->rk[r].tiled; ++shape) {
+          const int tt = kShapes[shape][0], trials = kShapes[shape][1], nt = kShapes[shape][2];
+          if ((o.flags & DD_FLAG_TILE256) && tt != 256) continue;
+          if ((o.flags & DD_FLAG_TRIALS32) && trials != 32) continue;
+          if ((o.flags & DD_FLAG_WARPS32) != 0 && nt != 1024) continue;
+          bool ok = false;
+          const int rc2 = plan_tiled_shape(&full[(size_t)p->row0[r] * p->Cp], ranges[r].n_trials,
+                                           p->Cp, ranges[r].decimation, tt, trials, nt,
+                                           &p->rk[r], &ok);
+          if (rc2) {
             free_plan(p);
-            return DD_ERR_NOMEM;
+            return rc2;
           }
-          cudaError_t e2 = cudaMemcpy(k.d_tabs, tp.tabs.data(), tp.tab_bytes,
-                                      cudaMemcpyHostToDevice);
-          if (e2 == cudaSuccess) e2 = ddk::prepare_tiled(u16, tt, tp.nstage, tp.smem);
-          if (e2 != cudaSuccess) {
-            free_plan(p);
-            return fail(DD_ERR_CUDA, "tiled kernel set-up: %s", cudaGetErrorString(e2));
-          }
-          k.tiled = true;
-          k.tt = tt;
-          k.nseg = tp.nseg;
-          k.nstage = tp.nstage;
-          k.row_slot = tp.row_slot;
-          k.zcap = tp.zcap;
-          k.smem = tp.smem;
-          k.lsu_wavefronts = tp.lsu_wavefronts;
-          k.copy_bytes = tp.copy_bytes;
-          break;
         }
       }
     }
@@ -768,6 +778,7 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     p->intervals.reserve(1 << 16);
   }
   DD_TRYCK(cudaDeviceSynchronize());
+  if (o.flags & DD_FLAG_AUTOTUNE) DD_TRY(ddk::plan_autotune(p));
 #undef DD_TRY
 #undef DD_TRYCK
   *out = p;
@@ -804,6 +815,9 @@ int dd_plan_model(dd_plan_t p, int32_t range, int64_t nout, dd_launch_model_t* o
   out->kind = k.tiled ? DD_KERNEL_TILED
                       : ((p->opts.flags & DD_FLAG_NAIVE) ? DD_KERNEL_PER_OUTPUT : DD_KERNEL_DIRECT);
   out->tile_samples = k.tiled ? k.tt : 0;
+  out->tile_trials = k.tiled ? k.trials : 0;
+  out->cta_threads = k.tiled ? k.threads : 0;
+  out->ctas_per_sm = k.tiled ? k.ctas : 0;
   out->outputs = (int64_t)R.n_trials * nout;
   out->adds = (double)out->outputs * p->C;
   int64_t smax = 0;
@@ -919,7 +933,7 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       A.nstage = K.nstage;
       A.tabs = K.d_tabs;
       A.err = p->err_word ? p->err_word : reinterpret_cast<int32_t*>(s.d_count + 1);
-      DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, st));
+      DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, K.trials, K.threads, st));
       p->launches += 1;
     } else if (p->opts.flags & DD_FLAG_NAIVE) {
       DD_CK(ddk::launch_dedisp_naive(R, p->Cp, st));
@@ -1063,13 +1077,16 @@ int dd_candidates(dd_plan_t p, int64_t seq, dd_cand_t* out, int64_t cap, int64_t
 }
 
 int dd_tiled_plan_check(const int32_t* shifts, int32_t n_trials, int32_t cpad,
-                        int32_t decimation, int32_t tile_samples, int32_t* ok,
-                        int64_t* violations) {
+                        int32_t decimation, int32_t tile_samples, int32_t tile_trials,
+                        int32_t* ok, int64_t* violations) {
   if (!shifts || !ok || !violations) return fail(DD_ERR_ARG, "NULL argument");
-  if (n_trials < 1 || cpad < 8 || cpad % 8 || (tile_samples != 256 && tile_samples != 512))
-    return fail(DD_ERR_ARG, "need n_trials >= 1, cpad a multiple of 8, tile_samples 256 or 512");
+  if (n_trials < 1 || cpad < 8 || cpad % 8 || (tile_samples != 256 && tile_samples != 512) ||
+      (tile_trials != 32 && tile_trials != 64))
+    return fail(DD_ERR_ARG, "need n_trials >= 1, cpad a multiple of 8, tile_samples 256 or 512, "
+                            "tile_trials 32 or 64");
   int k = 0;
-  *violations = ddk::tiled_plan_check(shifts, n_trials, cpad, decimation, tile_samples, &k);
+  *violations = ddk::tiled_plan_check(shifts, n_trials, cpad, decimation, tile_samples,
+                                      tile_trials, &k);
   *ok = k;
   return DD_OK;
 }

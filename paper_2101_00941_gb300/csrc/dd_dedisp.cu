@@ -1,8 +1,11 @@
 // Tiled brute-force dedispersion for sm_103a (Sec. 2.1 "dedispersion of data"; the sum is the
 // plain definition y[i][j] = sum_c x_d[c][j + s[i][c]], computed exactly in integers).
 //
-// One CTA (16 warps) owns a tile of kTileTrials consecutive DM trials x TT output samples of one
-// range and walks the channels in stages of kNG groups of eight channels.
+// One CTA owns a tile of D consecutive DM trials x TT output samples of one range and walks the
+// channels in stages of kNG groups of eight channels. Tile shapes (the plan picks the first that
+// fits, or times them all): 64 x 512 with 16 warps (128 registers per thread, 64 accumulators
+// per lane), the same tile with 32 warps (64 registers, 32 accumulators: twice the warps on the
+// same tables and shared memory), and 64 x 256 or 32 x 256 with 16 warps, two CTAs per SM.
 //
 //   * Delay classes. For an 8-channel group the tile's trials fall into a few classes by the
 //     relative delays (r0..r7) of the eight channels. A class shares one sequence of sums
@@ -44,10 +47,10 @@ namespace ddk {
 
 namespace {
 
-constexpr int kTileTrials = 64;
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
-constexpr int kTPW = kTileTrials / kWarps;  // trials per warp
+constexpr int kMaxTileTrials = 64;         // trials per tile: 64 or 32
+constexpr int kThreads = 512;               // threads of the 16-warp shapes
+constexpr int kWarps = kThreads / 32;       // work lists of a stage's build (one per warp, or
+                                            // shared by two warps in 32-warp CTAs)
 constexpr int kG = 8;                       // channels per group (one delay class)
 constexpr int kNG = 2;                      // groups per stage
 constexpr int kRows = kG * kNG;             // channel rows per stage
@@ -56,6 +59,12 @@ constexpr int kMaxCls = 16;                 // classes per group
 constexpr int kMaxWork = 8;                 // build ranges per warp and stage
 constexpr int kSegBytes = 128;              // inner extent of a staged-row copy (tensor map)
 constexpr size_t kSmemLimit = 220 * 1024;   // dynamic shared memory a CTA may plan for
+constexpr size_t kSmemLimit2 = 110 * 1024;  // ... when two CTAs share an SM
+
+// CTAs per SM a tile shape is compiled for (its register budget: 65536 / (NT x CTAs)).
+__host__ __device__ constexpr int tile_ctas(int D, int TT, int NT) {
+  return (NT == 1024 || (D == 64 && TT == 512)) ? 1 : 2;
+}
 
 // One delay class: its channels' first staged sample relative to the tile's first trial
 // (rel), and its pair words in the stage's word region.
@@ -67,7 +76,7 @@ struct ClsEntry {
 };
 
 struct GroupTab {
-  int16_t zstart[kTileTrials];  // stage word offset of each trial's sequence (0 for no trial)
+  int16_t zstart[kMaxTileTrials];  // stage word offset of each trial's sequence (0: no trial)
   ClsEntry cls[kMaxCls];
   int32_t ncls, pad0, pad1, pad2;
 };
@@ -333,19 +342,21 @@ __device__ __forceinline__ void pair_add(uint32_t z, uint32_t& even, uint32_t& o
   odd = __dp2a_lo(z, 0x0100u, odd);    // + high half
 }
 
-// Build every pair word of one stage: warp w walks its ranges of the plan's work list; lane l
-// builds unit 32 * b + l of every block b of a range, two blocks per pass.
-template <typename T>
+// Build every pair word of one stage: a warp walks the ranges of work list `list`; lane l builds
+// unit 32 * b + l of every block b of a range. With HALVES = 1 the warp builds every block, two
+// per pass; with HALVES = 2 two warps share the list, warp `half` building blocks b0 + half,
+// b0 + half + 2, ...
+template <typename T, int HALVES>
 __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& at, uint32_t rawb,
-                                            uint32_t* Zs, int warp, int lane) {
+                                            uint32_t* Zs, int list, int lane, int half) {
   constexpr int U = Word<T>::kUnit;
-  const int nw = tb.nwork[warp];
+  const int nw = tb.nwork[list];
   for (int w = 0; w < nw; ++w) {
-    const uint32_t wk = tb.work[warp][w];
+    const uint32_t wk = tb.work[list][w];
     const int gi = (int)((wk >> 4) & 1), p = (int)(wk & 15);
     const int b0 = (int)((wk >> 8) & 255), nb = (int)(wk >> 16);
     const int zlen = tb.g[gi].cls[p].zlen;
-    int u = 32 * b0 + lane;
+    int u = 32 * (b0 + (HALVES == 2 ? half : 0)) + lane;
     const uint4 ad = at.addr[gi][p];
     const uint2 sv = at.sh[gi][p];
     const uint32_t base = rawb + 4u * (uint32_t)u;  // one row word per unit
@@ -366,24 +377,38 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
     // even plane: pair words 0, 2, 4, ... of the class; odd plane: 1, 3, 5, ...
     uint32_t* ev = Zs + tb.g[gi].cls[p].zoff + (U / 2) * u;
     uint32_t* od = ev + zlen / 2;
-    for (int b = 0; b < nb; b += 2) {
-      if (u * U < zlen) Word<T>::template unit<0>(it, ev, od);
-      if (b + 1 < nb && (u + 32) * U < zlen)
-        Word<T>::template unit<128>(it, ev + 16 * U, od + 16 * U);
+    if (HALVES == 1) {
+      for (int b = 0; b < nb; b += 2) {
+        if (u * U < zlen) Word<T>::template unit<0>(it, ev, od);
+        if (b + 1 < nb && (u + 32) * U < zlen)
+          Word<T>::template unit<128>(it, ev + 16 * U, od + 16 * U);
 #pragma unroll
-      for (int k = 0; k < kG; ++k) it.addr[k] += 256u;  // 64 units further
-      u += 64;
-      ev += 32 * U;
-      od += 32 * U;
+        for (int k = 0; k < kG; ++k) it.addr[k] += 256u;  // 64 units further
+        u += 64;
+        ev += 32 * U;
+        od += 32 * U;
+      }
+    } else {
+      for (int b = half; b < nb; b += 2) {
+        if (u * U < zlen) Word<T>::template unit<0>(it, ev, od);
+#pragma unroll
+        for (int k = 0; k < kG; ++k) it.addr[k] += 256u;  // 64 units further
+        u += 64;
+        ev += 32 * U;
+        od += 32 * U;
+      }
     }
   }
 }
 
-template <typename T, int TT, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
+template <typename T, int TT, int NS, int D, int NT>
+__global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
     k_dedisp_tiled(const __grid_constant__ TiledArgs a) {
-  constexpr int KT = TT / 32;  // outputs per lane and trial
-  constexpr int KP = TT / 64;  // pair words per lane and trial
+  constexpr int KT = TT / 32;       // outputs per lane and trial
+  constexpr int KP = TT / 64;       // pair words per lane and trial
+  constexpr int W = NT / 32;        // warps
+  constexpr int kTPW = D / W;       // trials per warp
+  constexpr int HALVES = W / kWarps;  // warps sharing a build work list
   extern __shared__ __align__(1024) unsigned char smem[];  // tensor copies land 128-aligned
   const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap, NS);
   T* raw = reinterpret_cast<T*>(smem + SL.raw);
@@ -393,8 +418,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + SL.mbar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int trial0 = blockIdx.x * kTileTrials;
-  const int ntr = min(kTileTrials, a.n_trials - trial0);
+  const int trial0 = blockIdx.x * D;
+  const int ntr = min(D, a.n_trials - trial0);
   const int64_t j0 = (int64_t)blockIdx.y * TT;
   const int ngroups = a.cpad / kG;
   const int nstages = (ngroups + kNG - 1) / kNG;
@@ -421,14 +446,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   // (the same count in every thread)
   int issued = min(NS, nstages);
   int32_t xmin_next = 0;  // first delay of the next stage to issue (issuing thread)
-  if (tid == kThreads - 32) {
+  if (tid == NT - 32) {
     for (int s = 0; s < NS && s < nstages; ++s)
       issue_stage<T>(a, s, nstages, raw + (size_t)s * stage_elems, &tab[s], &mbar[s],
                      stage_xmin(a, s, nstages), j0);
     xmin_next = stage_xmin(a, NS, nstages);
   }
   bool ok0 = mbar_wait_bounded(&mbar[0], 0);
-  if (ok0) build_stage<T>(tab[0], atab[0], smem_addr(raw), Zbuf, warp, lane);
+  if (ok0) build_stage<T, HALVES>(tab[0], atab[0], smem_addr(raw), Zbuf, warp % kWarps, lane,
+                                  warp / kWarps);
   bool aborted = __syncthreads_or(!ok0);
   int s_abort = 0;  // first stage whose copies may still be in flight
 
@@ -445,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (s >= 1 && s + NS - 1 < nstages) {
       const int s2 = s + NS - 1;
       const int b2 = s2 % NS;
-      if (tid == kThreads - 32) {
+      if (tid == NT - 32) {
         issue_stage<T>(a, s2, nstages, raw + (size_t)b2 * stage_elems, &tab[b2], &mbar[b2],
                        xmin_next, j0);
         xmin_next = stage_xmin(a, s2 + 1, nstages);
@@ -463,8 +489,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int b1 = (s + 1) % NS;
       ok = mbar_wait_bounded(&mbar[b1], (uint32_t)(((s + 1) / NS) & 1));
       if (ok)
-        build_stage<T>(tab[b1], atab[(s + 1) & 1], smem_addr(raw + (size_t)b1 * stage_elems),
-                       Zbuf + (size_t)((s + 1) & 1) * a.zcap, warp, lane);
+        build_stage<T, HALVES>(tab[b1], atab[(s + 1) & 1],
+                               smem_addr(raw + (size_t)b1 * stage_elems),
+                               Zbuf + (size_t)((s + 1) & 1) * a.zcap, warp % kWarps, lane,
+                               warp / kWarps);
     }
     // (3) accumulate stage s: lane l of the warp reads, for each of its trials, pair word
     //     l + 32k of the trial's plane in both groups (outputs 2(l + 32k) and 2(l + 32k) + 1)
@@ -475,8 +503,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t* zq[kTPW];
 #pragma unroll
       for (int q = 0; q < kTPW; ++q) {
-        zp[q] = Zs + tc.g[0].zstart[warp + kWarps * q];
-        zq[q] = Zs + tc.g[1].zstart[warp + kWarps * q];
+        zp[q] = Zs + tc.g[0].zstart[warp + W * q];
+        zq[q] = Zs + tc.g[1].zstart[warp + W * q];
       }
       if (ng == kNG) {  // uniform; only the last stage may hold one group
 #pragma unroll
@@ -510,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // ---- epilogue: series + exact moments
 #pragma unroll
   for (int q = 0; q < kTPW; ++q) {
-    const int t = warp + kWarps * q;
+    const int t = warp + W * q;
     if (t < ntr) {
       int32_t* yr = a.y + (int64_t)(trial0 + t) * a.y_stride;
       unsigned long long s1 = 0, lo = 0, hi = 0;
@@ -552,18 +580,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <typename T, int TT, int NS>
+template <typename T, int TT, int NS, int D, int NT>
 cudaError_t launch_tiled_t(const TiledArgs& a, cudaStream_t st) {
   const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap, NS);
-  dim3 grid((unsigned)((a.n_trials + kTileTrials - 1) / kTileTrials),
-            (unsigned)((a.nout + TT - 1) / TT));
-  k_dedisp_tiled<T, TT, NS><<<grid, kThreads, SL.total, st>>>(a);
+  dim3 grid((unsigned)((a.n_trials + D - 1) / D), (unsigned)((a.nout + TT - 1) / TT));
+  k_dedisp_tiled<T, TT, NS, D, NT><<<grid, NT, SL.total, st>>>(a);
   return cudaGetLastError();
 }
 
 // Ranges sharing an instance need different amounts of shared memory, so the instance is
 // allowed the device's opt-in maximum once (a launch still only reserves what it asks for).
-template <typename T, int TT, int NS>
+template <typename T, int TT, int NS, int D, int NT>
 cudaError_t prepare_t(size_t smem) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -571,8 +598,14 @@ cudaError_t prepare_t(size_t smem) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   if (smem > (size_t)optin) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(k_dedisp_tiled<T, TT, NS>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(k_dedisp_tiled<T, TT, NS, D, NT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  // the whole unified L1 as shared memory, so that two CTAs of a two-CTA shape fit an SM
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dedisp_tiled<T, TT, NS, D, NT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 }  // namespace
@@ -628,12 +661,6 @@ cudaError_t launch_wait_selftest(int32_t* err, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int tiled_tile_samples(int is_u16, int choice) {
-  // preferred time tile first, a smaller one when the first does not fit shared memory
-  (void)is_u16;
-  return choice == 0 ? 512 : 256;
-}
-
 // Host: the shared-memory work of one row of time tiles, instruction by instruction as
 // k_dedisp_tiled issues it (one wavefront per warp-wide access: the kernel's loads and stores are
 // free of bank conflicts; a 64-bit store of 32 lanes is two wavefronts). Per (trial tile, stage):
@@ -646,21 +673,22 @@ int tiled_tile_samples(int is_u16, int choice) {
 //   copies       : the tensor copy of the 16 staged rows and the bulk copy of the stage table.
 static void tiled_smem_work(TiledPlan& P, int ntiles, int nstages, int ngroups, bool u16) {
   const StageTab* tabs = reinterpret_cast<const StageTab*>(P.tabs.data());
-  const int KP = P.tt / 64;
+  const int W = P.threads / 32, halves = W / kWarps;
+  const int KP = P.tt / 64, kTPW = P.trials / W;
   const int sts_per_block = u16 ? 2 : 4;
   int64_t lsu = 0, bytes = 0;
   for (int ti = 0; ti < ntiles; ++ti)
     for (int s = 0; s < nstages; ++s) {
       const StageTab& st = tabs[(size_t)ti * nstages + s];
       const int ng = std::min(kNG, ngroups - s * kNG);
-      lsu += (int64_t)kWarps * kTPW * KP * ng;        // accumulation words
-      lsu += (int64_t)kWarps * kTPW * ng;             // zstart entries
-      lsu += kWarps;                                  // nwork
+      lsu += (int64_t)W * kTPW * KP * ng;             // accumulation words
+      lsu += (int64_t)W * kTPW * ng;                  // zstart entries
+      lsu += W;                                       // nwork
       for (int w = 0; w < kWarps; ++w)
         for (int k = 0; k < st.nwork[w]; ++k) {
           const uint32_t wk = st.work[w][k];
           const int nb = (int)(wk >> 16);
-          lsu += 5;                                   // descriptor, zlen, zoff, addr, shift
+          lsu += 5 * halves;                          // descriptor, zlen, zoff, addr, shift
           lsu += (int64_t)nb * (2 * kG + sts_per_block);
         }
       lsu += (int64_t)(kAddrEntries / 32) * 2;        // addressing stores
@@ -679,12 +707,14 @@ static void tiled_smem_work(TiledPlan& P, int ntiles, int nstages, int ngroups, 
 // values up to 255 x decimation, so decimation must stay at or below 16; delays must be
 // monotone in the trial within a channel; classes, work lists and the staged rows must fit
 // their fixed-size tables and shared memory.
-TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int tt) {
+TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int tt, int D,
+                     int nt) {
   TiledPlan P;
   P.ok = false;
   const bool u16 = decimation > 1;
   if (decimation < 1 || kRows * 255 * decimation > 65535 || cpad % kG) return P;
-  const int D = kTileTrials, NG = kNG, U = u16 ? 2 : 4;
+  if ((D != 64 && D != 32) || (tt != 512 && tt != 256) || (nt != 512 && nt != 1024)) return P;
+  const int NG = kNG, U = u16 ? 2 : 4;
   const int ngroups = cpad / kG, nstages = (ngroups + NG - 1) / NG;
   const int ntiles = (ntr + D - 1) / D;
   int64_t spread = 0, zcap = 0, span = 0;
@@ -714,7 +744,7 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
         const int g = s * NG + gl;
         GroupTab& gt = st.g[gl];
         const int32_t* first = tab + (int64_t)t0 * cpad + kG * g;
-        int b[kTileTrials], cls_of[kTileTrials];
+        int b[kMaxTileTrials], cls_of[kMaxTileTrials];
         int32_t ckey[kMaxCls][kG];
         int cmin[kMaxCls], cmax[kMaxCls];
         int ncls = 0;
@@ -769,6 +799,9 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
   if (spread > 65536) return P;
   const int SEG = kSegBytes / (u16 ? 2 : 1);
   P.tt = tt;
+  P.trials = D;
+  P.threads = nt;
+  P.ctas = tile_ctas(D, tt, nt);
   // staged row: the stage's window (span + tt samples) from up to SEG - 1 samples into its
   // first segment, and 32 samples the word-wise build may read past the last word it uses
   P.nseg = (int)((span + tt + 32 + 2 * SEG - 2) / SEG);
@@ -781,19 +814,23 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
   // addressing entries hold byte offsets within a stage buffer as uint16
   if ((size_t)kRows * P.row_slot * (u16 ? 2 : 1) > 65535) return P;
   // as many staging buffers as fit (4, else 3: a copy is then issued two stages ahead)
+  const size_t limit = P.ctas == 2 ? kSmemLimit2 : kSmemLimit;
   for (int nst = kMaxNStage; nst >= 3 && !P.ok; --nst) {
     P.nstage = nst;
     P.smem = smem_layout(u16 ? 2 : 1, 4, P.row_slot, P.zcap, nst).total;
-    P.ok = P.smem <= kSmemLimit;
+    P.ok = P.smem <= limit;
   }
   if (P.ok) tiled_smem_work(P, ntiles, nstages, ngroups, u16);
   return P;
 }
 
-// Instances: uint8/uint16 data x 512/256-sample tiles x 4/3 staging buffers.
-#define DD_TILED_INSTANCES(X) \
-  X(uint8_t, 0, 512, 4) X(uint8_t, 0, 512, 3) X(uint8_t, 0, 256, 4) X(uint8_t, 0, 256, 3) \
-  X(uint16_t, 1, 512, 4) X(uint16_t, 1, 512, 3) X(uint16_t, 1, 256, 4) X(uint16_t, 1, 256, 3)
+// Instances: uint8/uint16 data x 4/3 staging buffers x the tile shapes (outputs, trials,
+// threads): 512 x 64 with 512 or 1024 threads, 256 x 64 and 256 x 32 with 512.
+#define DD_TILED_SHAPES(X, T, U16)                                                  \
+  X(T, U16, 512, 4, 64, 512) X(T, U16, 512, 3, 64, 512) X(T, U16, 512, 4, 64, 1024) \
+  X(T, U16, 512, 3, 64, 1024) X(T, U16, 256, 4, 64, 512) X(T, U16, 256, 3, 64, 512) \
+  X(T, U16, 256, 4, 32, 512) X(T, U16, 256, 3, 32, 512)
+#define DD_TILED_INSTANCES(X) DD_TILED_SHAPES(X, uint8_t, 0) DD_TILED_SHAPES(X, uint16_t, 1)
 
 // Host: plan one range and verify the tables against the delay table they were built from,
 // independently of how they were built. Returns the number of violations of:
@@ -804,19 +841,19 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
 //   - the stage's copy start is the smallest first-trial delay of its rows, and every read of
 //     every trial stays inside the staged row;
 //   - the build work lists cover every 32-unit block of every class exactly once.
-int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, int tt,
+int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, int tt, int D,
                          int* ok) {
-  const TiledPlan P = tiled_plan(tab, ntr, cpad, decimation, tt);
+  const TiledPlan P = tiled_plan(tab, ntr, cpad, decimation, tt, D, kThreads);
   *ok = P.ok ? 1 : 0;
   if (!P.ok) return 0;
   const bool u16 = decimation > 1;
   const int U = u16 ? 2 : 4, SEG = kSegBytes / (u16 ? 2 : 1);
   const int ngroups = cpad / kG, nstages = (ngroups + kNG - 1) / kNG;
-  const int ntiles = (ntr + kTileTrials - 1) / kTileTrials;
+  const int ntiles = (ntr + D - 1) / D;
   const StageTab* tabs = reinterpret_cast<const StageTab*>(P.tabs.data());
   int64_t bad = 0;
   for (int ti = 0; ti < ntiles; ++ti) {
-    const int t0 = ti * kTileTrials, n = std::min(kTileTrials, ntr - t0);
+    const int t0 = ti * D, n = std::min(D, ntr - t0);
     for (int s = 0; s < nstages; ++s) {
       const StageTab& st = tabs[(size_t)ti * nstages + s];
       int32_t xmin = INT32_MAX;
@@ -883,9 +920,10 @@ int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, 
   return bad;
 }
 
-cudaError_t prepare_tiled(int is_u16, int tt, int nstage, size_t smem) {
-#define DD_PREPARE(T, U16, TT, NS) \
-  if (is_u16 == U16 && tt == TT && nstage == NS) return prepare_t<T, TT, NS>(smem);
+cudaError_t prepare_tiled(int is_u16, int tt, int nstage, int D, int nt, size_t smem) {
+#define DD_PREPARE(T, U16, TT, NS, DT, NTH)                                     \
+  if (is_u16 == U16 && tt == TT && nstage == NS && D == DT && nt == NTH) \
+    return prepare_t<T, TT, NS, DT, NTH>(smem);
   DD_TILED_INSTANCES(DD_PREPARE)
 #undef DD_PREPARE
   return cudaErrorInvalidValue;
@@ -930,10 +968,12 @@ cudaError_t make_ring_map(CUtensorMap* map, const void* ring, int is_u16, int64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st) {
+cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, int D, int nt,
+                         cudaStream_t st) {
   if (a.nout <= 0 || a.n_trials <= 0) return cudaSuccess;
-#define DD_LAUNCH(T, U16, TT, NS) \
-  if (is_u16 == U16 && tt == TT && a.nstage == NS) return launch_tiled_t<T, TT, NS>(a, st);
+#define DD_LAUNCH(T, U16, TT, NS, DT, NTH)                                        \
+  if (is_u16 == U16 && tt == TT && a.nstage == NS && D == DT && nt == NTH) \
+    return launch_tiled_t<T, TT, NS, DT, NTH>(a, st);
   DD_TILED_INSTANCES(DD_LAUNCH)
 #undef DD_LAUNCH
   return cudaErrorInvalidValue;

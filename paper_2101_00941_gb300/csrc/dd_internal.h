@@ -86,6 +86,9 @@ struct TiledArgs {
 struct TiledPlan {
   bool ok = false;
   int tt = 0;
+  int trials = 0;          // trials per tile (64 or 32)
+  int threads = 0;         // threads per CTA (512 or 1024)
+  int ctas = 0;            // CTAs per SM the tile shape is compiled for
   int nseg = 0;            // 128-byte segments per staged channel row
   int nstage = 0;          // staging buffers
   int row_slot = 0;
@@ -101,15 +104,16 @@ struct TiledPlan {
   int64_t copy_bytes = 0;
 };
 
-int tiled_tile_samples(int is_u16, int choice);
-TiledPlan tiled_plan(const int32_t* shifts, int ntr, int cpad, int decimation, int tt);
+TiledPlan tiled_plan(const int32_t* shifts, int ntr, int cpad, int decimation, int tt,
+                     int trials, int threads);
 int64_t tiled_plan_check(const int32_t* shifts, int ntr, int cpad, int decimation, int tt,
-                         int* ok);
-cudaError_t prepare_tiled(int is_u16, int tt, int nstage, size_t smem);
+                         int trials, int* ok);
+cudaError_t prepare_tiled(int is_u16, int tt, int nstage, int trials, int threads, size_t smem);
 // One CTA waits, with the tiled kernel's bound, on a barrier nothing completes; sets *err bit 0
 // when the bound runs out.
 cudaError_t launch_wait_selftest(int32_t* err, cudaStream_t st);
-cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, cudaStream_t st);
+cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, int trials, int threads,
+                         cudaStream_t st);
 
 // Tensor map of a channel-major ring (uint8, or uint16 when is_u16) for the tiled kernel's
 // stage copies: dims {128-byte segment, segments per row, cpad rows}, box {segment, nseg, 16}.

@@ -9,6 +9,8 @@
 //   k_sps         : boxcar SNR over prefix sums + block peak finding (Sec. 2.2)
 #include <math.h>
 
+#include <algorithm>
+
 #include "dd_internal.h"
 
 namespace ddk {
@@ -144,47 +146,52 @@ cudaError_t launch_corner_turn(const uint8_t* in, int64_t n, int32_t nchans, uin
 
 // ------------------------------------------------------------------ decimation
 
-// out[c][m] = in[c][2m] + in[c][2m+1], four outputs per thread.
+// out[c][m] = in[c][2m] + in[c][2m+1], four outputs per thread. Channels c = blockIdx.y,
+// blockIdx.y + gridDim.y, ... (a grid dimension holds at most 65535 of them).
 __global__ void k_decimate_u8(const uint8_t* __restrict__ in, int64_t in_stride,
-                              uint16_t* __restrict__ out, int64_t out_stride, int64_t n_out) {
+                              uint16_t* __restrict__ out, int64_t out_stride, int64_t n_out,
+                              int32_t cpad) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t c = blockIdx.y;
   if (4 * k >= n_out) return;
-  const uint2 v = __ldg(reinterpret_cast<const uint2*>(in + c * in_stride + 8 * k));
-  const uint32_t lo = (v.x & 0xFFu) + ((v.x >> 8) & 0xFFu);
-  const uint32_t hi = ((v.x >> 16) & 0xFFu) + (v.x >> 24);
-  const uint32_t lo2 = (v.y & 0xFFu) + ((v.y >> 8) & 0xFFu);
-  const uint32_t hi2 = ((v.y >> 16) & 0xFFu) + (v.y >> 24);
-  uint2 o;
-  o.x = lo | (hi << 16);
-  o.y = lo2 | (hi2 << 16);
-  *reinterpret_cast<uint2*>(out + c * out_stride + 4 * k) = o;
+  for (int64_t c = blockIdx.y; c < cpad; c += gridDim.y) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(in + c * in_stride + 8 * k));
+    const uint32_t lo = (v.x & 0xFFu) + ((v.x >> 8) & 0xFFu);
+    const uint32_t hi = ((v.x >> 16) & 0xFFu) + (v.x >> 24);
+    const uint32_t lo2 = (v.y & 0xFFu) + ((v.y >> 8) & 0xFFu);
+    const uint32_t hi2 = ((v.y >> 16) & 0xFFu) + (v.y >> 24);
+    uint2 o;
+    o.x = lo | (hi << 16);
+    o.y = lo2 | (hi2 << 16);
+    *reinterpret_cast<uint2*>(out + c * out_stride + 4 * k) = o;
+  }
 }
 
 __global__ void k_decimate_u16(const uint16_t* __restrict__ in, int64_t in_stride,
-                               uint16_t* __restrict__ out, int64_t out_stride, int64_t n_out) {
+                               uint16_t* __restrict__ out, int64_t out_stride, int64_t n_out,
+                               int32_t cpad) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t c = blockIdx.y;
   if (4 * k >= n_out) return;
-  const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + c * in_stride + 8 * k));
-  const uint32_t s0 = (v.x & 0xFFFFu) + (v.x >> 16), s1 = (v.y & 0xFFFFu) + (v.y >> 16);
-  const uint32_t s2 = (v.z & 0xFFFFu) + (v.z >> 16), s3 = (v.w & 0xFFFFu) + (v.w >> 16);
-  uint2 o;
-  o.x = s0 | (s1 << 16);
-  o.y = s2 | (s3 << 16);
-  *reinterpret_cast<uint2*>(out + c * out_stride + 4 * k) = o;
+  for (int64_t c = blockIdx.y; c < cpad; c += gridDim.y) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + c * in_stride + 8 * k));
+    const uint32_t s0 = (v.x & 0xFFFFu) + (v.x >> 16), s1 = (v.y & 0xFFFFu) + (v.y >> 16);
+    const uint32_t s2 = (v.z & 0xFFFFu) + (v.z >> 16), s3 = (v.w & 0xFFFFu) + (v.w >> 16);
+    uint2 o;
+    o.x = s0 | (s1 << 16);
+    o.y = s2 | (s3 << 16);
+    *reinterpret_cast<uint2*>(out + c * out_stride + 4 * k) = o;
+  }
 }
 
 cudaError_t launch_decimate(const void* in, int in_is_u16, int64_t in_stride, uint16_t* out,
                             int64_t out_stride, int32_t cpad, int64_t n_out, cudaStream_t st) {
   if (n_out <= 0) return cudaSuccess;
-  dim3 grid((unsigned)(((n_out + 3) / 4 + 255) / 256), (unsigned)cpad);
+  dim3 grid((unsigned)(((n_out + 3) / 4 + 255) / 256), (unsigned)std::min(cpad, 65535));
   if (in_is_u16)
     k_decimate_u16<<<grid, 256, 0, st>>>(static_cast<const uint16_t*>(in), in_stride, out,
-                                         out_stride, n_out);
+                                         out_stride, n_out, cpad);
   else
     k_decimate_u8<<<grid, 256, 0, st>>>(static_cast<const uint8_t*>(in), in_stride, out,
-                                        out_stride, n_out);
+                                        out_stride, n_out, cpad);
   return cudaGetLastError();
 }
 

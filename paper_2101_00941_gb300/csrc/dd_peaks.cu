@@ -20,7 +20,7 @@ constexpr int kPeakThreads = 512;
 constexpr int kPeakCtasPerSm = 2;
 constexpr int kPeakIters = 2048;
 constexpr int kChains = 8;          // independent dependency chains per thread
-constexpr int kLdsWords = 2048;     // shared-memory words the load test walks over
+constexpr int kLdsWords = 4096;     // shared-memory words the load test reads (128 rows of 32)
 
 struct CtaTime {
   unsigned long long c0, c1, t0, t1;
@@ -60,6 +60,15 @@ __device__ __forceinline__ uint32_t lds_at(uint32_t addr) {
   return v;
 }
 
+// acc += the 32-bit words at base + 128 j, j = J .. 0 (immediate offsets).
+template <int J>
+__device__ __forceinline__ void lds_rows(uint32_t base, uint32_t& acc) {
+  acc += lds_at<128 * J>(base);
+  lds_rows<J - 1>(base, acc);
+}
+template <>
+__device__ __forceinline__ void lds_rows<-1>(uint32_t, uint32_t&) {}
+
 // Operations per thread of one kernel (each inner step is kChains operations).
 constexpr int kStepsPerIter = 8;
 constexpr long long kOpsPerThread = (long long)kPeakIters * kStepsPerIter * kChains;
@@ -67,14 +76,14 @@ constexpr long long kOpsPerThread = (long long)kPeakIters * kStepsPerIter * kCha
 template <int KIND>
 __global__ void __launch_bounds__(kPeakThreads, kPeakCtasPerSm)
     k_peak(uint32_t seed, uint32_t* sink, CtaTime* times) {
-  __shared__ uint32_t buf[kLdsWords + 32 * 16];
+  __shared__ uint32_t buf[kLdsWords];
   const int tid = threadIdx.x;
   uint32_t a[kChains];
 #pragma unroll
   for (int i = 0; i < kChains; ++i) a[i] = seed * (uint32_t)(2 * i + 1) + (uint32_t)tid;
   const uint32_t b = seed ^ 0x00010001u;
   if (KIND == kLds) {
-    for (int k = tid; k < kLdsWords + 32 * 16; k += kPeakThreads) buf[k] = seed + (uint32_t)k;
+    for (int k = tid; k < kLdsWords; k += kPeakThreads) buf[k] = seed + (uint32_t)k;
   }
   __syncthreads();
   CtaTime ct;
@@ -84,19 +93,15 @@ __global__ void __launch_bounds__(kPeakThreads, kPeakCtasPerSm)
   }
   __syncthreads();
   if (KIND == kLds) {
-    // lane l of a warp reads word l + 32 j of a 128-byte-aligned row: 32 consecutive words,
-    // one wavefront per load; the base moves through the buffer so no two loads are alike
+    // lane l of a warp reads word l of a 128-byte row: 32 consecutive words, one wavefront per
+    // load. The kStepsPerIter * kChains loads of an iteration read distinct consecutive rows at
+    // immediate offsets from one base (no address arithmetic per load, and no two loads alike),
+    // and the base moves from one iteration to the next.
     const uint32_t base0 = (uint32_t)__cvta_generic_to_shared(buf) + 4u * (uint32_t)(tid & 31);
     uint32_t acc = a[0];
     for (int it = 0; it < kPeakIters; ++it) {
-      const uint32_t base = base0 + 128u * (uint32_t)((it * 7 + (tid >> 5)) & (kLdsWords / 32 - 1));
-#pragma unroll
-      for (int s = 0; s < kStepsPerIter; ++s) {
-        // kChains loads per step, 128 bytes apart
-        acc ^= lds_at<0>(base + 1024u * (uint32_t)(s & 1)) + lds_at<128>(base) +
-               lds_at<256>(base) + lds_at<384>(base) + lds_at<512>(base) + lds_at<640>(base) +
-               lds_at<768>(base) + lds_at<896>(base);
-      }
+      const uint32_t base = base0 + 128u * ((uint32_t)(it * 7 + (tid >> 5)) & 63u);
+      lds_rows<kStepsPerIter * kChains - 1>(base, acc);
     }
     a[0] = acc;
   } else {

@@ -207,6 +207,31 @@ def test_tiled_kernel_256_sample_tiles():
     assert check(w, x, [4096] * 3 + [2048], 2, flags=dd.DD_FLAG_TILE256) >= 0
 
 
+@pytest.mark.parametrize("flags,shape", [
+    (dd.DD_FLAG_WARPS32, (512, 64, 1024)),          # 32 warps on the 64 x 512 tile
+    (dd.DD_FLAG_TILE256, (256, 64, 512)),           # two CTAs per SM
+    (dd.DD_FLAG_TILE256 | dd.DD_FLAG_TRIALS32, (256, 32, 512)),
+    (dd.DD_FLAG_AUTOTUNE, None),                    # whichever shape the timing picks
+])
+def test_tiled_kernel_tile_shapes(flags, shape):
+    """Every tile shape of the tiled kernel, forced by the testing flags or picked by the plan's
+    autotuner, on every trial of ranges x1 .. x16 in ragged chunks: series, moments and
+    candidates against the oracle."""
+    w = _tiled_regime(nsamp=1 << 14)
+    w.ranges = w.ranges[:5]
+    plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), 4096, n_streams=1, flags=flags)
+    try:
+        for r in range(len(w.ranges)):
+            m = plan.model(r, 1)
+            assert m["kind"] == dd.DD_KERNEL_TILED
+            if shape is not None:
+                assert (m["tile_samples"], m["tile_trials"], m["cta_threads"]) == shape
+    finally:
+        plan.close()
+    x = w.generate(_arrivals(w))
+    assert check(w, x, [4096] * 3 + [2048], 2, flags=flags) >= 0
+
+
 def test_tiled_kernel_odd_output_counts():
     """Windows of odd length: x1 ranges only, so the overlap is the largest delay (63 samples),
     and chunks of 4096, 4096, 2047 and 1001 samples give windows of 4033, 4096, 2047 and 1001

@@ -27,20 +27,28 @@ def _tables(w):
     return out
 
 
-@pytest.mark.parametrize("tt", [512, 256])
-def test_4096_channel_plan(tt):
+SHAPES = [(512, 64), (256, 64), (256, 32)]
+
+
+@pytest.mark.parametrize("tt,trials", SHAPES)
+def test_4096_channel_plan(tt, trials):
     w = configs.mid(nsamp=1 << 17)
     for tab, r in zip(_tables(w), w.ranges):
-        ok, bad = dd.dd_tiled_plan_check(tab, r.decimation, tt)
+        ok, bad = dd.dd_tiled_plan_check(tab, r.decimation, tt, trials)
         assert (ok, bad) == (1, 0), r
 
 
-def test_8192_channel_plan_edges():
+@pytest.mark.parametrize("tt,trials", SHAPES)
+def test_8192_channel_plan_edges(tt, trials):
     w = configs.out_of_core(nsamp=1 << 20)
     tabs = _tables(w)
     for k in (0, len(w.ranges) - 1):  # x1 and the widest, x16
-        ok, bad = dd.dd_tiled_plan_check(tabs[k], w.ranges[k].decimation, 512)
-        assert (ok, bad) == (1, 0), w.ranges[k]
+        ok, bad = dd.dd_tiled_plan_check(tabs[k], w.ranges[k].decimation, tt, trials)
+        assert bad == 0, w.ranges[k]
+        # a two-CTA shape must fit half an SM's shared memory: the 64 x 256 tile of this plan's
+        # x1 range does not (117 KB), the 32 x 256 tile does
+        if k == 0:
+            assert ok == (0 if (tt, trials) == (256, 64) else 1)
 
 
 def test_ragged_channels_and_trial_tiles():
@@ -53,9 +61,10 @@ def test_ragged_channels_and_trial_tiles():
     w = configs.mid(nsamp=1 << 15, nchans=4096, ranges=ranges)
     w.nchans, w.foff = 1001, -300.0 / 1024
     for tab, r in zip(_tables(w), w.ranges):
-        ok, bad = dd.dd_tiled_plan_check(tab, r.decimation, 512)
-        assert bad == 0
-        assert ok == (1 if r.decimation <= 16 else 0), r
+        for tt, trials in SHAPES:
+            ok, bad = dd.dd_tiled_plan_check(tab, r.decimation, tt, trials)
+            assert bad == 0
+            assert ok == (1 if r.decimation <= 16 else 0), (r, tt, trials)
 
 
 def test_odd_group_count():
