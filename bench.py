@@ -604,14 +604,17 @@ def main(args):
     xd = xh.cuda()
     dchunks = [xd[k % nring] for k in range(nchunks)]
     hchunks = [xh[k % nring] for k in range(nchunks)]
+    t_plan = time.perf_counter()
     plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=w.n_streams,
-                   max_width=max(w.widths), peak_block=32, device=dev, flags=dd.DD_FLAG_TIMING)
+                   max_width=max(w.widths), peak_block=32, device=dev,
+                   flags=dd.DD_FLAG_TIMING | dd.DD_FLAG_AUTOTUNE)
+    t_plan = time.perf_counter() - t_plan
     O = plan.O
+    shapes = [plan.model(r, 1) for r in range(len(w.ranges))]
     peaks = dd.dd_measure_peaks(dev)
     with ClockSampler(dev) as clk:
         ms, ncand, launches, dd_ms, dd_n = time_steps(plan, dchunks, w, args.steps, args.warmup,
                                                       barrier)
-    range_ms = [plan.stats_range(r) for r in range(len(w.ranges))]
     T0 = args.warmup * w.nsamp  # stream position of the timed steps
     sizes = [L] * nchunks * args.steps
     outs = outputs_of_chunks(w, O, T0, sizes)
@@ -619,6 +622,18 @@ def main(args):
     lat = []
     ms_e2e, ncand_e2e, _, _, _ = time_steps(plan, hchunks, w, args.steps, args.warmup, barrier,
                                             lat)
+    # each range's launches alone: two chunks (full windows) on one stream, so no launch of
+    # another range or chunk overlaps them
+    solo = torch.cuda.Stream()
+    plan.sync()
+    plan.stats(reset=True)
+    T_solo = (2 * args.warmup + 2 * args.steps) * w.nsamp
+    for k in range(2):
+        plan.run(dchunks[k % len(dchunks)], L, cuda_stream=solo.cuda_stream)
+        plan.search(w.widths, w.threshold)
+    plan.sync()
+    range_ms = [plan.stats_range(r) for r in range(len(w.ranges))]
+    _, per_solo = launch_model(plan, w, O, T_solo, [L, L])
     plan.close()
     if world > 1:
         ms, ms_e2e = rank_max([ms, ms_e2e], "cuda")
@@ -635,10 +650,12 @@ def main(args):
     bpo = dram_traffic_per_output(w)
     per_range = []
     for r, (rms, rn) in enumerate(range_ms):
-        p = per[r]
+        p = per_solo[r]
         rs = rms * 1e-3
+        m = shapes[r]
         per_range.append({
             "decimation": w.ranges[r].decimation, "launches": rn, "ms": rms,
+            "tile": [m["tile_trials"], m["tile_samples"], m["cta_threads"], m["ctas_per_sm"]],
             "adds_per_s": p["adds"] / rs if rs > 0 else None,
             "frac": p["adds"] / rs / peak_int if rs > 0 else None,
             "frac_smem": (p["smem_wavefronts"] + p["copy_bytes"] / 128.0) / rs / peak_wf
@@ -686,6 +703,10 @@ def main(args):
                          "timed launches over their union time, against measured conflict-free "
                          "32-bit load wavefronts per SM-clock x SMs x clock",
             "per_range": per_range,
+            "per_range_note": "each range's launches timed alone (two chunks on one stream); "
+                              "tile = [trials, outputs, threads per CTA, CTAs per SM] chosen by "
+                              "the plan's autotuner",
+            "plan_s": t_plan,
             "measured_peaks": peaks},
         "clocks": clocks,
     }

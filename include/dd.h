@@ -237,6 +237,30 @@ int dd_moments(dd_plan_t plan, int32_t range, const dd_moments_t** dev_ptr, int6
 int sps_run(dd_plan_t plan, const int32_t* widths, int32_t nwidths, float threshold);
 
 /*
+ * sps_run_ex -- sps_run with a choice of noise statistic (Sec. 2.2 names the SPDT estimators of
+ * the search without defining them; both choices here are readings).
+ *   how->estimator  : DD_EST_WINDOW: the chunk window's mean and deviation of the series, with
+ *                     sqrt(w) scaling (sps_run; how may be NULL for it);
+ *                     DD_EST_CLIPPED: per boxcar width, the mean and population deviation of the
+ *                     boxcar sums B_w themselves, made robust by clip_iters steps of
+ *                     kappa-sigma clipping: each step keeps the sums within
+ *                     ceil(mu - kappa*sd) .. floor(mu + kappa*sd) of the previous step's (FP64
+ *                     mu = T1/N, sd = sqrt(N*T2 - T1^2)/N from exact integer sums). The SNR is
+ *                     (N*B - T1) / sqrt(N*T2 - T1^2); a width with no variance left gives none.
+ *   how->clip_iters : 0 .. 16 clipping steps;  how->clip_kappa : the bound in deviations (> 0)
+ * Errors: those of sps_run; DD_ERR_ARG for an unknown estimator or bad clipping parameters.
+ */
+#define DD_EST_WINDOW 0
+#define DD_EST_CLIPPED 1
+typedef struct {
+  int32_t estimator;
+  int32_t clip_iters;
+  double clip_kappa;
+} dd_sps_opts_t;
+int sps_run_ex(dd_plan_t plan, const int32_t* widths, int32_t nwidths, float threshold,
+               const dd_sps_opts_t* how);
+
+/*
  * dd_candidates -- wait for chunk `seq`'s search and copy its candidates.
  *   seq    : chunk number (0-based dd_run call count); must be one of the last n_streams chunks
  *   out    : caller-owned host array of cap entries, sorted by (range, trial, t_start, width)

@@ -30,6 +30,8 @@ DD_FLAG_TILE256 = 8
 DD_FLAG_TRIALS32 = 16
 DD_FLAG_AUTOTUNE = 32
 DD_FLAG_WARPS32 = 64
+DD_EST_WINDOW = 0
+DD_EST_CLIPPED = 1
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
 
@@ -39,7 +41,8 @@ EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_selftest_wait",
            "dd_serve_poll", "dd_serve_pending", "dd_serve_destroy", "dd_batch_create",
            "dd_batch_run", "dd_batch_wait", "dd_batch_info", "dd_batch_candidates",
            "dd_batch_destroy", "dd_plan_destroy", "dd_last_error", "dd_moments",
-           "dd_plan_model", "dd_measure_peaks", "dd_stats_range", "dd_group_candidates")
+           "dd_plan_model", "dd_measure_peaks", "dd_stats_range", "dd_group_candidates",
+           "sps_run_ex")
 
 
 class dd_range_t(ctypes.Structure):
@@ -74,6 +77,11 @@ GROUP_DTYPE = np.dtype([("rep", "<i8"), ("members", "<i8"), ("dm_lo", "<f8"), ("
                         ("t_lo", "<i8"), ("t_hi", "<i8")])
 
 MOMENTS_DTYPE = np.dtype([("s1", "<i8"), ("s2lo", "<u8"), ("s2hi", "<u8"), ("pad", "<u8")])
+
+
+class dd_sps_opts_t(ctypes.Structure):
+    _fields_ = [("estimator", ctypes.c_int32), ("clip_iters", ctypes.c_int32),
+                ("clip_kappa", ctypes.c_double)]
 
 
 class dd_batch_beam_t(ctypes.Structure):
@@ -118,6 +126,7 @@ def lib() -> ctypes.CDLL:
         L.dd_run.argtypes = [vp, vp, i64, vp]
         L.dd_series.argtypes = [vp, i32, P(vp), P(i64), P(i64), P(i64)]
         L.sps_run.argtypes = [vp, vp, i32, f32]
+        L.sps_run_ex.argtypes = [vp, vp, i32, f32, P(dd_sps_opts_t)]
         L.dd_candidates.argtypes = [vp, i64, vp, i64, P(i64), i64]
         L.dd_sync.argtypes = [vp]
         L.dd_stats.argtypes = [vp, P(i64), P(f64), P(i64), i32]
@@ -266,6 +275,15 @@ def sps_run(plan: int, widths, threshold: float):
     _check(lib().sps_run(plan, w.ctypes.data, w.size, ctypes.c_float(threshold)))
 
 
+def sps_run_ex(plan: int, widths, threshold: float, estimator: int = DD_EST_WINDOW,
+               clip_iters: int = 3, clip_kappa: float = 3.0):
+    """sps_run with a choice of noise statistic (see dd.h)."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    o = dd_sps_opts_t(int(estimator), int(clip_iters), float(clip_kappa))
+    _check(lib().sps_run_ex(plan, w.ctypes.data, w.size, ctypes.c_float(threshold),
+                            ctypes.byref(o)))
+
+
 def dd_candidates(plan: int, seq: int, cap: int = 1 << 20, timeout_ms: int = 0) -> np.ndarray:
     out = np.zeros(cap, dtype=CAND_DTYPE)
     n = ctypes.c_int64()
@@ -344,8 +362,11 @@ class Plan:
         self.seq += 1
         return self.seq
 
-    def search(self, widths, threshold):
-        sps_run(self.h, widths, threshold)
+    def search(self, widths, threshold, estimator=None, clip_iters=3, clip_kappa=3.0):
+        if estimator is None:
+            sps_run(self.h, widths, threshold)
+        else:
+            sps_run_ex(self.h, widths, threshold, estimator, clip_iters, clip_kappa)
 
     def candidates(self, seq=None, cap=1 << 20, timeout_ms=0):
         return dd_candidates(self.h, self.seq if seq is None else seq, cap, timeout_ms)

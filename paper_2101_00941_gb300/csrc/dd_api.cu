@@ -144,6 +144,7 @@ struct Slot {
   uint16_t* ringd[9] = {};      // level l >= 1 (decimation 2^l): [Cp][Rd[l]]
   int32_t* series = nullptr;    // every range, at series_off[r]
   ddk::Moments* mom = nullptr;  // [total trials]
+  ddk::WidthStats* wst = nullptr;  // [total trials][kMaxWidths] clipped statistics
   dd_cand_t* cands = nullptr;   // [max_cands]
   unsigned long long* d_count = nullptr;  // [0] candidates, [1] kernel error bits
   unsigned long long* h_count = nullptr;  // pinned copy of d_count
@@ -236,6 +237,7 @@ void free_plan(dd_plan_s* p) {
     for (auto* r : s.ringd) cudaFree(r);
     cudaFree(s.series);
     cudaFree(s.mom);
+    cudaFree(s.wst);
     cudaFree(s.cands);
     cudaFree(s.d_count);
     cudaFreeHost(s.h_count);
@@ -750,6 +752,8 @@ int dd_plan(const double* freqs_mhz, int32_t nchans, double tsamp_s, const dd_ra
     }
     DD_TRY(dalloc(&s.series, sizeof(int32_t) * (size_t)p->series_elems, "series"));
     DD_TRY(dalloc(&s.mom, sizeof(ddk::Moments) * (size_t)total_rows, "moments"));
+    DD_TRY(dalloc(&s.wst, sizeof(ddk::WidthStats) * (size_t)total_rows * ddk::kMaxWidths,
+                  "clipped statistics"));
     DD_TRY(dalloc(&s.cands, sizeof(dd_cand_t) * (size_t)p->opts.max_cands, "candidates"));
     DD_TRY(dalloc(&s.d_count, 2 * sizeof(unsigned long long), "count"));
     DD_TRYCK(cudaMemset(s.d_count, 0, 2 * sizeof(unsigned long long)));
@@ -985,7 +989,8 @@ int dd_moments(dd_plan_t p, int32_t range, const dd_moments_t** dev_ptr, int64_t
   return DD_OK;
 }
 
-int sps_run(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold) {
+int sps_run_ex(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold,
+               const dd_sps_opts_t* how) {
   if (!p) return fail(DD_ERR_ARG, "plan is NULL");
   if (!widths || nwidths < 1 || nwidths > ddk::kMaxWidths)
     return fail(DD_ERR_ARG, "nwidths must be 1..%d", ddk::kMaxWidths);
@@ -996,6 +1001,12 @@ int sps_run(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold
       return fail(DD_ERR_ARG, "widths must be strictly increasing");
   }
   if (!std::isfinite(threshold)) return fail(DD_ERR_ARG, "threshold must be finite");
+  const bool clipped = how && how->estimator == DD_EST_CLIPPED;
+  if (how && how->estimator != DD_EST_WINDOW && !clipped)
+    return fail(DD_ERR_ARG, "unknown estimator %d", how->estimator);
+  if (clipped && (how->clip_iters < 0 || how->clip_iters > 16 || !(how->clip_kappa > 0) ||
+                  !std::isfinite(how->clip_kappa)))
+    return fail(DD_ERR_ARG, "clipping needs 0 <= clip_iters <= 16 and a finite clip_kappa > 0");
   if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
   Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
   if (s.searched) return fail(DD_ERR_STATE, "the latest chunk was already searched");
@@ -1024,6 +1035,23 @@ int sps_run(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold
     a.cands = s.cands;
     a.count = s.d_count;
     a.cap = p->opts.max_cands;
+    if (clipped) {
+      ddk::ClipArgs c;
+      std::memset(&c, 0, sizeof c);
+      c.y = a.y;
+      c.stride = a.stride;
+      c.n = a.n;
+      c.n_trials = a.n_trials;
+      c.nw = a.nw;
+      for (int k = 0; k < a.nw; ++k) c.wd[k] = a.wd[k];
+      c.hist = a.hist;
+      c.iters = how->clip_iters;
+      c.kappa = how->clip_kappa;
+      c.out = s.wst + (int64_t)p->row0[r] * ddk::kMaxWidths;
+      DD_CK(ddk::launch_clip_stats(c, st));
+      p->launches += 1;
+      a.wst = c.out;
+    }
     DD_CK(ddk::launch_sps(a, st));
     p->launches += 1;
   }
@@ -1033,6 +1061,10 @@ int sps_run(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold
   DD_CK(cudaEventRecord(s.ev_free, st));
   s.searched = true;
   return DD_OK;
+}
+
+int sps_run(dd_plan_t p, const int32_t* widths, int32_t nwidths, float threshold) {
+  return sps_run_ex(p, widths, nwidths, threshold, nullptr);
 }
 
 int dd_candidates(dd_plan_t p, int64_t seq, dd_cand_t* out, int64_t cap, int64_t* ncands,

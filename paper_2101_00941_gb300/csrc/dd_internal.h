@@ -20,6 +20,27 @@ struct Moments {
 };
 static_assert(sizeof(Moments) == sizeof(dd_moments_t), "dd_moments views the device records");
 
+// Clipped statistics of one (trial, width) boxcar series: N values, T1 = their sum, T2 = the sum
+// of their squares as 128 bits (t2lo, t2hi). 32 bytes.
+struct WidthStats {
+  long long n, t1;
+  unsigned long long t2lo, t2hi;
+};
+
+// One launch of the clipped-statistics kernel: every trial of one range of one chunk.
+struct ClipArgs {
+  const int32_t* y;        // [n_trials][stride]
+  int64_t stride;
+  int64_t n;               // window length
+  int32_t n_trials;
+  int32_t nw;
+  int32_t wd[kMaxWidths];  // decimated widths, increasing
+  int32_t hist;            // largest decimated width - 1, rounded up to 256
+  int32_t iters;           // clipping steps
+  double kappa;            // clipping bound in deviations
+  WidthStats* out;         // [n_trials][nw]
+};
+
 // Per-range parameters of the delay-table kernel.
 struct ShiftRange {
   double dm_start, dm_step;
@@ -45,6 +66,7 @@ struct SpsArgs {
   dd_cand_t* cands;
   unsigned long long* count;
   int64_t cap;
+  const WidthStats* wst;   // [n_trials][nw] per-width statistics; nullptr: the window's moments
 };
 
 // Per-range geometry of one chunk for the tiled dedispersion kernel.
@@ -162,5 +184,6 @@ cudaError_t launch_dedisp_direct(const DedispRange& r, int32_t cpad, cudaStream_
 cudaError_t launch_moments(const int32_t* y, int32_t ntr, int64_t n, int64_t stride, Moments* mom,
                            cudaStream_t st);
 cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st);
+cudaError_t launch_clip_stats(const ClipArgs& a, cudaStream_t st);
 
 }  // namespace ddk

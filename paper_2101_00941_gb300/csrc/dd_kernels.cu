@@ -442,6 +442,59 @@ __device__ __forceinline__ uint4 prefix4(const uint32_t* P, int idx, int w) {
   return make_uint4(a.w, b.x, b.y, b.z);
 }
 
+// One pass of the search kernels over window samples seg0 .. seg0 + kSpsSeg - 1 of series yi
+// (zero past n): this lane's four 4-sample chunks (samples seg0 + q0 + 128 g + e) are loaded and
+// turned into uint32 prefix sums continuing from P[H] (the sum through the sample before the
+// pass), returned in v and stored to P[1 + H + q]. Two CTA barriers; P[0 .. H] must be in place.
+__device__ __forceinline__ void sps_pass_prefix(const int32_t* __restrict__ yi, bool vec,
+                                                long long n, long long seg0, int q0, int lane,
+                                                int wid, int H, uint32_t* P, uint32_t* warp_tot,
+                                                uint32_t (&v)[4][4]) {
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const long long j = seg0 + q0 + 128 * g;
+    if (vec && j + 4 <= n) {
+      const int4 t = __ldg(reinterpret_cast<const int4*>(yi + j));
+      v[g][0] = (uint32_t)t.x;
+      v[g][1] = (uint32_t)t.y;
+      v[g][2] = (uint32_t)t.z;
+      v[g][3] = (uint32_t)t.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[g][e] = (j + e < n) ? (uint32_t)__ldg(yi + j + e) : 0u;
+    }
+  }
+  uint32_t run = 0;  // sum of this warp's chunks before the current one (lanes, then g)
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    v[g][1] += v[g][0];
+    v[g][2] += v[g][1];
+    v[g][3] += v[g][2];
+    uint32_t incl = v[g][3];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    const uint32_t pre = run + incl - v[g][3];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[g][e] += pre;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) warp_tot[wid] = run;
+  __syncthreads();  // warp totals; the history entries P[0 .. H] of this pass
+  uint32_t base = P[H];  // sum through the sample before the pass
+  for (int k = 0; k < wid; ++k) base += warp_tot[k];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[g][e] += base;  // now prefix sums through each sample
+    *reinterpret_cast<uint4*>(P + 1 + H + q0 + 128 * g) =
+        make_uint4(v[g][0], v[g][1], v[g][2], v[g][3]);
+  }
+  __syncthreads();  // the pass's prefix sums
+}
+
 // One CTA per trial; passes of kSpsSeg window samples. Warp v owns pass samples
 // 512v .. 512v + 511, lane l the 4-sample chunks 512v + 128g + 4l (g = 0..3). P holds uint32
 // prefix sums of the pass and of the H samples before it (entry 1 + H + q = sum through window
@@ -455,35 +508,61 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
   extern __shared__ __align__(16) uint32_t Ps[];
   uint32_t* P = Ps + kSpsPad;  // [1 + hist + kSpsSeg]
   __shared__ double den[kMaxWidths];
+  __shared__ long long ca[kMaxWidths], cb[kMaxWidths];
   __shared__ uint32_t bthr[kMaxWidths];
   __shared__ uint32_t warp_tot[kSpsThreads / 32];
 
   const int32_t i = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const Moments m = a.mom[i];
   const long long n = a.n;
   if (n <= 0) return;
-  const long long s1 = (long long)m.s1;
-  // V = n*S2 - S1^2 in 128 bits (exact; S1 >= 0 because every series value is a sum of
-  // non-negative samples)
-  const unsigned long long un = (unsigned long long)n, us1 = (unsigned long long)s1;
-  const unsigned long long p_lo = un * m.s2lo;
-  const unsigned long long p_hi = __umul64hi(un, m.s2lo) + un * m.s2hi;
-  const unsigned long long q_lo = us1 * us1, q_hi = __umul64hi(us1, us1);
-  const unsigned long long v_lo = p_lo - q_lo;
-  const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
-  if (v_lo == 0 && v_hi == 0) return;  // constant series: no candidates
-  const double sq = sqrt(u128_to_f64(v_hi, v_lo));
   const double thr = (double)a.threshold;
-  if (tid < a.nw) {
-    const int w = a.wd[tid];
-    den[tid] = sqrt((double)w) * sq;
-    // SNR >= thr  <=>  B >= (w*S1 + thr*den) / n; the bound keeps a margin of 2 + 1e-9 relative
-    // so that rounding in this estimate can never reject a block the exact test accepts. As a
-    // uint32 bound on boxcar sums (< 2^31): at or below 0 every sum passes, above 2^32 - 1 none.
-    const double t = ((double)w * (double)s1 + thr * den[tid]) / (double)n;
+  // Per width k: SNR = (ca[k] * B - cb[k]) / den[k]. Window statistics: ca = n, cb = w * S1,
+  // den = sqrt(w) * sqrt(n * S2 - S1^2). Clipped per-width statistics (a.wst): ca = N_k,
+  // cb = T1_k, den = sqrt(N_k * T2_k - T1_k^2). A width with den 0 gives no candidates.
+  if (a.wst == nullptr) {
+    const Moments m = a.mom[i];
+    const long long s1 = (long long)m.s1;
+    // V = n*S2 - S1^2 in 128 bits (exact; S1 >= 0 because every series value is a sum of
+    // non-negative samples)
+    const unsigned long long un = (unsigned long long)n, us1 = (unsigned long long)s1;
+    const unsigned long long p_lo = un * m.s2lo;
+    const unsigned long long p_hi = __umul64hi(un, m.s2lo) + un * m.s2hi;
+    const unsigned long long q_lo = us1 * us1, q_hi = __umul64hi(us1, us1);
+    const unsigned long long v_lo = p_lo - q_lo;
+    const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
+    if (v_lo == 0 && v_hi == 0) return;  // constant series: no candidates
+    const double sq = sqrt(u128_to_f64(v_hi, v_lo));
+    if (tid < a.nw) {
+      const int w = a.wd[tid];
+      den[tid] = sqrt((double)w) * sq;
+      ca[tid] = n;
+      cb[tid] = (long long)w * s1;
+      // SNR >= thr  <=>  B >= (w*S1 + thr*den) / n; the bound keeps a margin of 2 + 1e-9
+      // relative so that rounding in this estimate can never reject a block the exact test
+      // accepts. As a uint32 bound on boxcar sums (< 2^31): at or below 0 every sum passes,
+      // above 2^32 - 1 none.
+      const double t = ((double)w * (double)s1 + thr * den[tid]) / (double)n;
+      const double tl = t - 2.0 - 1e-9 * fabs(t);
+      bthr[tid] = tl <= 0.0 ? 0u : (tl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(tl));
+    }
+  } else if (tid < a.nw) {
+    const WidthStats st = a.wst[(int64_t)i * a.nw + tid];
+    const unsigned long long un = (unsigned long long)st.n, ut1 = (unsigned long long)st.t1;
+    const unsigned long long p_lo = un * st.t2lo;
+    const unsigned long long p_hi = __umul64hi(un, st.t2lo) + un * st.t2hi;
+    const unsigned long long q_lo = ut1 * ut1, q_hi = __umul64hi(ut1, ut1);
+    const unsigned long long v_lo = p_lo - q_lo;
+    const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
+    const bool live = st.n > 0 && (v_lo | v_hi) != 0;
+    den[tid] = live ? sqrt(u128_to_f64(v_hi, v_lo)) : 0.0;
+    ca[tid] = st.n;
+    cb[tid] = st.t1;
+    // SNR >= thr  <=>  B >= (T1 + thr*den) / N, with the margin above
+    const double t = live ? ((double)st.t1 + thr * den[tid]) / (double)st.n : 0.0;
     const double tl = t - 2.0 - 1e-9 * fabs(t);
-    bthr[tid] = tl <= 0.0 ? 0u : (tl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(tl));
+    bthr[tid] = !live ? 0xFFFFFFFFu
+                      : (tl <= 0.0 ? 0u : (tl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(tl)));
   }
   const int H = a.hist;
   const int nw = a.nw;
@@ -496,51 +575,8 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
   for (int k = tid; k <= H; k += kSpsThreads) P[k] = 0;
 
   for (long long seg0 = 0; seg0 < n; seg0 += kSpsSeg) {
-    // ---- this lane's four chunks (zero past the window) and their prefix sums
     uint32_t v[4][4];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const long long j = seg0 + q0 + 128 * g;
-      if (vec && j + 4 <= n) {
-        const int4 t = __ldg(reinterpret_cast<const int4*>(yi + j));
-        v[g][0] = (uint32_t)t.x;
-        v[g][1] = (uint32_t)t.y;
-        v[g][2] = (uint32_t)t.z;
-        v[g][3] = (uint32_t)t.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[g][e] = (j + e < n) ? (uint32_t)__ldg(yi + j + e) : 0u;
-      }
-    }
-    uint32_t run = 0;  // sum of this warp's chunks before the current one (lanes, then g)
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      v[g][1] += v[g][0];
-      v[g][2] += v[g][1];
-      v[g][3] += v[g][2];
-      uint32_t incl = v[g][3];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += o;
-      }
-      const uint32_t pre = run + incl - v[g][3];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) v[g][e] += pre;
-      run += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) warp_tot[wid] = run;
-    __syncthreads();  // warp totals; the history entries P[0 .. H] of this pass
-    uint32_t base = P[H];  // sum through the sample before the pass
-    for (int k = 0; k < wid; ++k) base += warp_tot[k];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) v[g][e] += base;  // now prefix sums through each sample
-      *reinterpret_cast<uint4*>(P + 1 + H + q0 + 128 * g) =
-          make_uint4(v[g][0], v[g][1], v[g][2], v[g][3]);
-    }
-    __syncthreads();  // the pass's prefix sums
+    sps_pass_prefix(yi, vec, n, seg0, q0, lane, wid, H, P, warp_tot, v);
 
     // ---- filter: every boxcar sum of this lane's samples against the bounds
     const long long wj0 = seg0 + wid * 512;  // the warp's first sample
@@ -586,12 +622,12 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
       bool have = false;
       for (int k = 0; k < nw; ++k) {
         const int w = a.wd[k];
-        const bool valid = (j < n) && (j >= w - 1);
+        const bool valid = (j < n) && (j >= w - 1) && den[k] != 0.0;
         const uint32_t bw = valid ? pj - P[1 + H + q - w] : 0u;
         int off;
         const int best = block_argmax(bw, valid, B, lane, off);
         if (leader && best >= 0) {
-          const long long num = n * (long long)best - (long long)w * s1;
+          const long long num = ca[k] * (long long)best - cb[k];
           const double snr = (double)num / den[k];
           const long long jk = j + off;  // the leader holds the block's first sample
           if (!have || snr > bs || (snr == bs && jk < bj)) {
@@ -620,6 +656,148 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
     // the last H + 1 entries become the next pass's history (P[kSpsSeg] = sum before it)
     for (int k = tid; k <= H; k += kSpsThreads) P[k] = P[kSpsSeg + k];
   }
+}
+
+// Clipped statistics of every boxcar series of one trial (one CTA per trial): for each width w,
+// the values B_w[j] (window samples j >= w - 1) are summed over the whole window (step 0:
+// count, sum, 128-bit sum of squares), then, for up to `iters` steps, again over the values
+// within ceil(mu - kappa*sd) .. floor(mu + kappa*sd) of the previous step's mean and population
+// deviation (FP64, one rounding per operation, as the oracle). A width whose previous step has no
+// values or no variance keeps its statistics. Each step sweeps the series once per group of
+// kClipGroup widths, forming the boxcar sums from the carried prefix sums of the search kernel.
+constexpr int kClipGroup = 8;
+
+__global__ void __launch_bounds__(kSpsThreads) k_clip_stats(const ClipArgs a) {
+  extern __shared__ __align__(16) uint32_t Ps[];
+  uint32_t* P = Ps + kSpsPad;  // [1 + hist + kSpsSeg]
+  __shared__ uint32_t warp_tot[kSpsThreads / 32];
+  __shared__ double lo_b[kMaxWidths], hi_b[kMaxWidths];
+  __shared__ int live[kMaxWidths];
+  __shared__ WidthStats st[kMaxWidths];
+  __shared__ unsigned long long red[kClipGroup][4][kSpsThreads / 32];
+
+  const int32_t i = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const long long n = a.n;
+  const int nw = a.nw, H = a.hist;
+  const int32_t* yi = a.y + (int64_t)i * a.stride;
+  const bool vec = (reinterpret_cast<uintptr_t>(yi) & 15) == 0;
+  const int q0 = wid * 512 + 4 * lane;
+  if (tid < kMaxWidths) {
+    lo_b[tid] = -1.0;  // step 0: every value (all boxcar sums are >= 0)
+    hi_b[tid] = 1e300;
+    live[tid] = tid < nw ? 1 : 0;
+    st[tid] = WidthStats{0, 0, 0, 0};
+  }
+  __syncthreads();
+  for (int step = 0; step <= a.iters; ++step) {
+    for (int g0 = 0; g0 < nw; g0 += kClipGroup) {
+      bool any = false;
+      for (int k = g0; k < min(nw, g0 + kClipGroup); ++k) any |= live[k] != 0;
+      if (!any) continue;  // uniform: every thread reads the same flags
+      uint32_t cn[kClipGroup];
+      unsigned long long c1[kClipGroup], c2l[kClipGroup], c2h[kClipGroup];
+#pragma unroll
+      for (int kk = 0; kk < kClipGroup; ++kk) cn[kk] = 0, c1[kk] = c2l[kk] = c2h[kk] = 0;
+      for (int k = tid; k <= H; k += kSpsThreads) P[k] = 0;  // samples before the window
+      for (long long seg0 = 0; seg0 < n; seg0 += kSpsSeg) {
+        uint32_t v[4][4];
+        sps_pass_prefix(yi, vec, n, seg0, q0, lane, wid, H, P, warp_tot, v);
+#pragma unroll
+        for (int kk = 0; kk < kClipGroup; ++kk) {
+          const int k = g0 + kk;
+          const bool on = k < nw && live[min(k, kMaxWidths - 1)];
+          const int w = on ? a.wd[k] : 1;
+          const double lo = on ? lo_b[k] : 1.0, hi = on ? hi_b[k] : 0.0;  // empty when off
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int idx = 1 + H + q0 + 128 * g;
+            const uint4 s4 = prefix4(P, idx, w);
+            const long long j = seg0 + q0 + 128 * g;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const uint32_t b = v[g][e] - (e == 0 ? s4.x : e == 1 ? s4.y : e == 2 ? s4.z : s4.w);
+              const double bd = (double)b;
+              if (j + e < n && j + e >= w - 1 && bd >= lo && bd <= hi) {
+                const unsigned long long sq = (unsigned long long)b * b;
+                cn[kk] += 1;
+                c1[kk] += b;
+                c2l[kk] += sq;
+                c2h[kk] += (c2l[kk] < sq) ? 1ull : 0ull;
+              }
+            }
+          }
+        }
+        __syncthreads();  // every read of this pass's P is done
+        for (int k = tid; k <= H; k += kSpsThreads) P[k] = P[kSpsSeg + k];
+      }
+      // block sums of the group's widths: warp butterflies, then one lane per width
+#pragma unroll
+      for (int kk = 0; kk < kClipGroup; ++kk) {
+        unsigned long long x0 = cn[kk], x1 = c1[kk], lo = c2l[kk], hi = c2h[kk];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          x0 += __shfl_xor_sync(0xffffffffu, x0, off);
+          x1 += __shfl_xor_sync(0xffffffffu, x1, off);
+          const unsigned long long olo = __shfl_xor_sync(0xffffffffu, lo, off);
+          const unsigned long long ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+          const unsigned long long nlo = lo + olo;
+          hi = hi + ohi + (nlo < lo ? 1ull : 0ull);
+          lo = nlo;
+        }
+        if (lane == 0) {
+          red[kk][0][wid] = x0;
+          red[kk][1][wid] = x1;
+          red[kk][2][wid] = lo;
+          red[kk][3][wid] = hi;
+        }
+      }
+      __syncthreads();
+      if (tid < kClipGroup && g0 + tid < nw && live[g0 + tid]) {
+        unsigned long long x0 = 0, x1 = 0, lo = 0, hi = 0;
+        for (int q = 0; q < kSpsThreads / 32; ++q) {
+          x0 += red[tid][0][q];
+          x1 += red[tid][1][q];
+          const unsigned long long nlo = lo + red[tid][2][q];
+          hi = hi + red[tid][3][q] + (nlo < lo ? 1ull : 0ull);
+          lo = nlo;
+        }
+        st[g0 + tid] = WidthStats{(long long)x0, (long long)x1, lo, hi};
+      }
+      __syncthreads();
+    }
+    // bounds of the next step from this step's statistics
+    if (step < a.iters && tid < nw && live[tid]) {
+      const WidthStats s = st[tid];
+      const unsigned long long un = (unsigned long long)s.n, ut1 = (unsigned long long)s.t1;
+      const unsigned long long p_lo = un * s.t2lo;
+      const unsigned long long p_hi = __umul64hi(un, s.t2lo) + un * s.t2hi;
+      const unsigned long long q_lo = ut1 * ut1, q_hi = __umul64hi(ut1, ut1);
+      const unsigned long long v_lo = p_lo - q_lo;
+      const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
+      if (s.n == 0 || (v_lo | v_hi) == 0) {
+        live[tid] = 0;
+      } else {
+        const double dn = __ll2double_rn(s.n);
+        const double mu = __ddiv_rn(__ll2double_rn(s.t1), dn);
+        const double sd = __ddiv_rn(__dsqrt_rn(u128_to_f64(v_hi, v_lo)), dn);
+        const double ks = __dmul_rn(a.kappa, sd);
+        lo_b[tid] = ceil(__dsub_rn(mu, ks));
+        hi_b[tid] = floor(__dadd_rn(mu, ks));
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < nw) a.out[(int64_t)i * nw + tid] = st[tid];
+}
+
+cudaError_t launch_clip_stats(const ClipArgs& a, cudaStream_t st) {
+  if (a.n <= 0 || a.n_trials <= 0 || a.nw <= 0) return cudaSuccess;
+  if (a.hist < 0 || a.hist % 4 || a.hist + 1 > kSpsSeg || a.iters < 0 || !(a.kappa > 0))
+    return cudaErrorInvalidValue;
+  const size_t smem = sizeof(uint32_t) * (size_t)(kSpsPad + 1 + a.hist + kSpsSeg);
+  k_clip_stats<<<a.n_trials, kSpsThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st) {

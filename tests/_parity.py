@@ -29,8 +29,9 @@ def oracle_trial_snr(y: np.ndarray, j: int, w: int) -> float:
 
 
 def compare_candidates(gpu: np.ndarray, ref: np.ndarray, threshold: float, block: int,
-                       series_of=None, J0_of=None, d_of=None):
-    """Assert the candidate lists agree (see module doc). Returns the number of matched blocks."""
+                       series_of=None, J0_of=None, d_of=None, trial_snr=oracle_trial_snr):
+    """Assert the candidate lists agree (see module doc). Returns the number of matched blocks.
+    trial_snr(y, j, w) scores an alternative pick (default: the window-statistics SNR)."""
     def key(c, J0, d):
         wd = int(c["width"]) // d
         jend = int(c["t_start"]) // d + wd - 1 - J0
@@ -62,9 +63,18 @@ def compare_candidates(gpu: np.ndarray, ref: np.ndarray, threshold: float, block
             y = series_of(r, tr)
             wd = int(a["width"]) // d
             j = int(a["t_start"]) // d + wd - 1 - J0
-            alt = oracle_trial_snr(y, j, wd)
+            alt = trial_snr(y, j, wd)
             assert abs(alt - b["snr"]) <= SNR_RTOL * abs(b["snr"]), (a, b, alt)
     return len(set(g) & set(o))
+
+
+def clipped_trial_snr(kappa: float, iters: int):
+    """SNR of a trailing boxcar under the clipped per-width statistics (oracle.clipped_moments)."""
+    def snr(y: np.ndarray, j: int, w: int) -> float:
+        N, T1, T2 = oracle.clipped_moments(y, w, kappa, iters)
+        b = int(y[j - w + 1:j + 1].astype(np.int64).sum())
+        return (N * b - T1) / math.sqrt(float(N * T2 - T1 * T1))
+    return snr
 
 
 def assert_moments_equal(got, want, what=""):
