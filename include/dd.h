@@ -434,9 +434,14 @@ int dd_serve_poll(dd_server_t server, dd_serve_result_t* out, int32_t max, int32
  * its own streams), so the beams' work overlaps on the device; every (beam, chunk) keeps its own
  * candidates. DD_BATCH_GRAPH captures the step once as a CUDA graph that every dd_batch_run
  * replays (the inputs stay at their device addresses; refill them between steps).
- * DD_BATCH_AUTOTUNE picks the time tile of every plan's ranges by timing the candidates. */
+ * DD_BATCH_AUTOTUNE picks the tile shape of every plan's ranges by timing the candidates.
+ * DD_BATCH_PERSISTENT runs the step in rounds on one stream instead: round c takes chunk c of
+ * every beam that has one (copies, corner turns, decimations), then ONE persistent dedispersion
+ * launch per kernel instance (uint8 / uint16 data) whose CTAs, one per SM, take (beam, range,
+ * trial tile, time tile) items from a device work list until it is empty, then the searches. */
 #define DD_BATCH_GRAPH 1u
 #define DD_BATCH_AUTOTUNE 2u
+#define DD_BATCH_PERSISTENT 4u
 
 typedef struct dd_batch_s* dd_batch_t;
 

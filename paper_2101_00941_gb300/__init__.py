@@ -34,6 +34,7 @@ DD_EST_WINDOW = 0
 DD_EST_CLIPPED = 1
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
+DD_BATCH_PERSISTENT = 4
 
 EXPORTS = ("dd_plan", "dd_plan_info", "dd_plan_kernel", "dd_selftest_wait",
            "dd_tiled_plan_check", "dd_run", "dd_series", "sps_run", "dd_candidates", "dd_sync",
@@ -483,7 +484,7 @@ class Batch:
 
     def __init__(self, beams, ranges, chunk_len, widths, threshold, n_streams=1,
                  max_width=None, peak_block=32, cap_per_chunk=1 << 14, graph=False,
-                 autotune=False, device=0, flags=DD_FLAG_DEVICE_INPUT):
+                 autotune=False, persistent=False, device=0, flags=DD_FLAG_DEVICE_INPUT):
         self._freqs = [np.ascontiguousarray(f, dtype=np.float64) for f, _, _ in beams]
         self._inputs = [x for _, _, x in beams]
         arr = (dd_batch_beam_t * len(beams))()
@@ -496,7 +497,8 @@ class Batch:
         o = dd_opts_t(int(chunk_len), int(n_streams), int(max_width or int(w.max())),
                       int(peak_block), int(device), 0, int(flags), 0)
         h = ctypes.c_void_p()
-        bf = (DD_BATCH_GRAPH if graph else 0) | (DD_BATCH_AUTOTUNE if autotune else 0)
+        bf = ((DD_BATCH_GRAPH if graph else 0) | (DD_BATCH_AUTOTUNE if autotune else 0) |
+              (DD_BATCH_PERSISTENT if persistent else 0))
         _check(lib().dd_batch_create(len(beams), ctypes.addressof(arr), ctypes.addressof(rr),
                                      len(ranges), ctypes.byref(o), w.ctypes.data, w.size,
                                      ctypes.c_float(threshold), int(cap_per_chunk), bf,

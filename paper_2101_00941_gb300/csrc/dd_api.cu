@@ -837,7 +837,11 @@ int dd_plan_model(dd_plan_t p, int32_t range, int64_t nout, dd_launch_model_t* o
   return DD_OK;
 }
 
-int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) {
+// dd_run's work; with `defer`, the tiled launches of the 64 x 512 x 512 shape are not made but
+// handed back (argument block and instance) for a persistent launch the caller makes later on
+// the same stream.
+static int run_impl(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream,
+                    std::vector<ddk::DeferredTile>* defer) {
   if (!p) return fail(DD_ERR_ARG, "plan is NULL");
   if (!chunk) return fail(DD_ERR_ARG, "chunk is NULL");
   if (nsamp <= 0 || nsamp > p->L || nsamp % p->dmax != 0)
@@ -937,8 +941,17 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
       A.nstage = K.nstage;
       A.tabs = K.d_tabs;
       A.err = p->err_word ? p->err_word : reinterpret_cast<int32_t*>(s.d_count + 1);
-      DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, K.trials, K.threads, st));
-      p->launches += 1;
+      if (defer && K.tt == 512 && K.trials == 64 && K.threads == 512) {
+        ddk::DeferredTile dt;
+        dt.args = A;
+        dt.is_u16 = R.is_u16;
+        dt.nstage = K.nstage;
+        dt.smem = K.smem;
+        defer->push_back(dt);
+      } else {
+        DD_CK(ddk::launch_tiled(A, R.is_u16, K.tt, K.trials, K.threads, st));
+        p->launches += 1;
+      }
     } else if (p->opts.flags & DD_FLAG_NAIVE) {
       DD_CK(ddk::launch_dedisp_naive(R, p->Cp, st));
     } else {
@@ -962,6 +975,10 @@ int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) 
   p->T_total += nsamp;
   p->next_seq += 1;
   return DD_OK;
+}
+
+int dd_run(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda_stream) {
+  return run_impl(p, chunk, nsamp, cuda_stream, nullptr);
 }
 
 int dd_series(dd_plan_t p, int32_t range, const int32_t** dev_ptr, int64_t* len, int64_t* stride,
@@ -1199,3 +1216,10 @@ int dd_stats_range(dd_plan_t p, int32_t range, double* dedisp_ms, int64_t* dedis
 void dd_plan_destroy(dd_plan_t p) { free_plan(p); }
 
 }  // extern "C"
+
+namespace ddk {
+int run_deferred(dd_plan_s* p, const uint8_t* chunk, int64_t nsamp, cudaStream_t st,
+                 std::vector<DeferredTile>* out) {
+  return run_impl(p, chunk, nsamp, st, out);
+}
+}  // namespace ddk

@@ -1,10 +1,18 @@
 // Batched execution: many beams of uneven length and channel count, each with a plan of its
 // own, processed from their first sample in one enqueued step (Sec. 1: time chunks over CUDA
-// streams, applied across beams). Chunks are enqueued round-robin over the beams, so different
-// beams' work overlaps on the device; every (beam, chunk) has its own candidate buffer, so one
-// step keeps every result. Optionally the whole step is captured once as a CUDA graph and
-// replayed (the beams' inputs stay at the same device addresses; each step starts again at
-// sample 0), and the time tile of each plan's ranges is chosen by timing the candidates.
+// streams, applied across beams). Every (beam, chunk) has its own candidate buffer, so one step
+// keeps every result. Two ways to run a step:
+//   streams    : chunks are enqueued round-robin over the beams, each beam on its own streams,
+//                so different beams' launches overlap on the device;
+//   persistent : (DD_BATCH_PERSISTENT) round c takes chunk c of every beam that has one, on one
+//                stream: the beams' copies, corner turns and decimations, then ONE persistent
+//                dedispersion launch per instance (uint8 / uint16 data, staging buffers) whose
+//                CTAs, one per SM, take (beam, range, trial tile, time tile) items from a device
+//                work list until it is empty, then every beam's search.
+// Optionally the whole step is captured once as a CUDA graph and replayed (the beams' inputs
+// stay at the same device addresses; each step starts again at sample 0; the persistent work
+// lists are copied from pinned host memory written when the step was captured), and every
+// plan's tile shapes are chosen by timing the candidates.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -38,6 +46,17 @@ struct dd_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool counts_ready = false;
+  // persistent mode: per round, the deferred tiled launches' argument blocks and the work-list
+  // segments of each instance, in pinned host memory and on the device
+  int64_t rounds = 0, max_descs = 0;
+  ddk::TiledArgs* h_descs = nullptr;   // [rounds][max_descs]
+  ddk::TiledArgs* d_descs = nullptr;
+  int32_t* h_segd = nullptr;           // [rounds][max_descs] descriptor of each segment
+  int32_t* d_segd = nullptr;
+  int64_t* h_segf = nullptr;           // [rounds][max_descs + 4] segment firsts per instance
+  int64_t* d_segf = nullptr;
+  unsigned long long* d_counters = nullptr;  // [rounds][4]
+  int sms = 0;
 };
 
 namespace {
@@ -55,6 +74,13 @@ void free_batch(dd_batch_s* b) {
   if (b->root) cudaStreamDestroy(b->root);
   cudaFree(b->d_cands);
   cudaFree(b->d_counts);
+  cudaFreeHost(b->h_descs);
+  cudaFree(b->d_descs);
+  cudaFreeHost(b->h_segd);
+  cudaFree(b->d_segd);
+  cudaFreeHost(b->h_segf);
+  cudaFree(b->d_segf);
+  cudaFree(b->d_counters);
   cudaFreeHost(b->h_counts);
   cudaFreeHost(b->h_cands);
   delete b;
@@ -101,6 +127,108 @@ int enqueue_step(dd_batch_s* b) {
                             cudaMemcpyDeviceToHost, b->root),
             "count readback");
   return rc;
+}
+
+// One step in persistent mode, every launch on the root stream (see the file comment).
+int enqueue_step_persistent(dd_batch_s* b) {
+  int rc = ck(cudaMemsetAsync(b->d_counts + b->total_chunks, 0, sizeof(unsigned long long),
+                              b->root),
+              "error word");
+  const int64_t L = b->chunk_len;
+  std::vector<ddk::DeferredTile> defs;
+  for (int64_t c = 0; rc == DD_OK && c < b->rounds; ++c) {
+    defs.clear();
+    for (size_t i = 0; rc == DD_OK && i < b->plans.size(); ++i) {
+      if (c >= b->nchunks[i]) continue;
+      const int64_t n = std::min(L, b->nsamp[i] - c * L);
+      rc = ddk::run_deferred(b->plans[i], b->inputs[i] + (size_t)(c * L) * b->nchans[i], n,
+                             b->root, &defs);
+    }
+    if (rc) break;
+    if ((int64_t)defs.size() > b->max_descs)
+      return ddk::report_error(DD_ERR_STATE, "dd_batch: more deferred launches than planned");
+    // the round's work lists: one per instance (uint8/uint16 x 3/4 staging buffers), each a run
+    // of segments (one per deferred launch: all its tiles)
+    ddk::TiledArgs* hd = b->h_descs + c * b->max_descs;
+    int32_t* hs = b->h_segd + c * b->max_descs;
+    int64_t* hf = b->h_segf + c * (b->max_descs + 4);
+    for (size_t k = 0; k < defs.size(); ++k) hd[k] = defs[k].args;
+    int nseg_total = 0;
+    int64_t fpos = 0;
+    struct Inst {
+      int is_u16, nstage, nseg, seg0;
+      int64_t f0;
+      size_t smem;
+    };
+    std::vector<Inst> insts;
+    for (int u16 = 0; u16 < 2; ++u16)
+      for (int ns = 3; ns <= 4; ++ns) {
+        Inst in{u16, ns, 0, nseg_total, fpos, 0};
+        int64_t first = 0;
+        for (size_t k = 0; k < defs.size(); ++k) {
+          if (defs[k].is_u16 != u16 || defs[k].nstage != ns) continue;
+          const ddk::TiledArgs& a = defs[k].args;
+          const int64_t tiles = (int64_t)((a.n_trials + 63) / 64) * ((a.nout + 511) / 512);
+          hs[nseg_total + in.nseg] = (int32_t)k;
+          hf[fpos + in.nseg] = first;
+          first += tiles;
+          in.smem = std::max(in.smem, defs[k].smem);
+          in.nseg += 1;
+        }
+        if (in.nseg == 0) continue;
+        hf[fpos + in.nseg] = first;
+        nseg_total += in.nseg;
+        fpos += in.nseg + 1;
+        insts.push_back(in);
+      }
+    if (defs.empty()) continue;
+    ddk::TiledArgs* dd_ = b->d_descs + c * b->max_descs;
+    int32_t* ds = b->d_segd + c * b->max_descs;
+    int64_t* df = b->d_segf + c * (b->max_descs + 4);
+    rc = ck(cudaMemcpyAsync(dd_, hd, sizeof(ddk::TiledArgs) * defs.size(), cudaMemcpyHostToDevice,
+                            b->root),
+            "work list");
+    if (rc == DD_OK)
+      rc = ck(cudaMemcpyAsync(ds, hs, sizeof(int32_t) * nseg_total, cudaMemcpyHostToDevice,
+                              b->root),
+              "work list");
+    if (rc == DD_OK)
+      rc = ck(cudaMemcpyAsync(df, hf, sizeof(int64_t) * fpos, cudaMemcpyHostToDevice, b->root),
+              "work list");
+    if (rc == DD_OK)
+      rc = ck(cudaMemsetAsync(b->d_counters + 4 * c, 0, 4 * sizeof(unsigned long long), b->root),
+              "counters");
+    for (size_t g = 0; rc == DD_OK && g < insts.size(); ++g) {
+      const Inst& in = insts[g];
+      ddk::PersistArgs pa;
+      pa.descs = dd_;
+      pa.seg_desc = ds + in.seg0;
+      pa.seg_first = df + in.f0;
+      pa.nseg = in.nseg;
+      pa.pad = 0;
+      pa.counter = b->d_counters + 4 * c + g;
+      rc = ck(ddk::launch_tiled_persistent(pa, in.is_u16, 512, in.nstage, 64, 512, in.smem,
+                                           b->sms, b->root),
+              "persistent dedispersion");
+    }
+    for (size_t i = 0; rc == DD_OK && i < b->plans.size(); ++i) {
+      if (c >= b->nchunks[i]) continue;
+      const int64_t slot = b->first[i] + c;
+      rc = ddk::sps_enqueue(b->plans[i], b->widths.data(), (int32_t)b->widths.size(),
+                            b->threshold, b->d_cands + slot * b->cap, b->d_counts + slot,
+                            b->cap);
+    }
+  }
+  if (rc == DD_OK)
+    rc = ck(cudaMemcpyAsync(b->h_counts, b->d_counts,
+                            sizeof(unsigned long long) * (b->total_chunks + 1),
+                            cudaMemcpyDeviceToHost, b->root),
+            "count readback");
+  return rc;
+}
+
+int step(dd_batch_s* b) {
+  return (b->flags & DD_BATCH_PERSISTENT) ? enqueue_step_persistent(b) : enqueue_step(b);
 }
 
 int reset_all(dd_batch_s* b) {
@@ -184,6 +312,28 @@ int dd_batch_create(int32_t nbeams, const dd_batch_beam_t* beams, const dd_range
     cudaGetLastError();
     rc = ddk::report_error(DD_ERR_NOMEM, "dd_batch_create: pinned buffers");
   }
+  if (rc == DD_OK && (flags & DD_BATCH_PERSISTENT)) {
+    for (auto n : b->nchunks) b->rounds = std::max(b->rounds, n);
+    b->max_descs = (int64_t)b->plans.size() * nranges;
+    const size_t nd = (size_t)(b->rounds * b->max_descs);
+    const size_t nf = (size_t)(b->rounds * (b->max_descs + 4));
+    if (cudaMallocHost(&b->h_descs, sizeof(ddk::TiledArgs) * std::max<size_t>(nd, 1)) !=
+            cudaSuccess ||
+        cudaMallocHost(&b->h_segd, sizeof(int32_t) * std::max<size_t>(nd, 1)) != cudaSuccess ||
+        cudaMallocHost(&b->h_segf, sizeof(int64_t) * std::max<size_t>(nf, 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_descs, sizeof(ddk::TiledArgs) * std::max<size_t>(nd, 1)) !=
+            cudaSuccess ||
+        cudaMalloc(&b->d_segd, sizeof(int32_t) * std::max<size_t>(nd, 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_segf, sizeof(int64_t) * std::max<size_t>(nf, 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_counters, sizeof(unsigned long long) * 4 *
+                                       std::max<size_t>((size_t)b->rounds, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = ddk::report_error(DD_ERR_NOMEM, "dd_batch_create: persistent work lists");
+    }
+    if (rc == DD_OK)
+      rc = ck(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device),
+              "multiprocessor count");
+  }
   if (rc == DD_OK)
     for (auto p : b->plans)
       ddk::plan_redirect_errors(p, reinterpret_cast<int32_t*>(b->d_counts + b->total_chunks));
@@ -193,7 +343,7 @@ int dd_batch_create(int32_t nbeams, const dd_batch_beam_t* beams, const dd_range
     if (rc == DD_OK)
       rc = ck(cudaStreamBeginCapture(b->root, cudaStreamCaptureModeRelaxed), "begin capture");
     if (rc == DD_OK) {
-      rc = enqueue_step(b);
+      rc = step(b);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(b->root, &g);
       if (rc == DD_OK) rc = ck(e, "end capture");
@@ -217,7 +367,7 @@ int dd_batch_run(dd_batch_t b) {
     rc = ck(cudaGraphLaunch(b->exec, b->root), "graph launch");
   } else if (rc == DD_OK) {
     rc = reset_all(b);
-    if (rc == DD_OK) rc = enqueue_step(b);
+    if (rc == DD_OK) rc = step(b);
   }
   if (rc == DD_OK) rc = ck(cudaEventRecord(b->done, b->root), "record");
   return rc;

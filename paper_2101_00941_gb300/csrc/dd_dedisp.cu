@@ -109,10 +109,13 @@ struct SmemLayout {
   size_t raw, z, tab, addr, mbar, total;
 };
 
+// The mbarriers come first, at the same place for every tile shape and range (a persistent CTA
+// re-initialises them between tiles of different ranges); the staged rows start 128-byte aligned.
 __host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot, int zcap,
                                                   int nst) {
   SmemLayout L;
-  size_t off = 0;
+  L.mbar = 0;
+  size_t off = 128;
   L.raw = off;
   off = align16(off + (size_t)nst * kRows * row_slot * es);
   L.z = off;
@@ -121,8 +124,6 @@ __host__ __device__ inline SmemLayout smem_layout(int es, int zes, int row_slot,
   off = align16(off + sizeof(StageTab) * nst);
   L.addr = off;
   off = align16(off + sizeof(AddrTab) * 2);
-  L.mbar = off;
-  off = align16(off + sizeof(unsigned long long) * nst);
   L.total = off;
   return L;
 }
@@ -194,10 +195,10 @@ __device__ __forceinline__ int64_t first_seg(const TiledArgs& a, int64_t j0, int
   return (a.m0 + j0 + xmin) / SEG;
 }
 
-__device__ __forceinline__ int32_t stage_xmin(const TiledArgs& a, int stage, int nstages) {
+__device__ __forceinline__ int32_t stage_xmin(const TiledArgs& a, int stage, int nstages,
+                                              int tile) {
   if (stage >= nstages) return 0;
-  return __ldg(&reinterpret_cast<const StageTab*>(a.tabs)[(size_t)blockIdx.x * nstages + stage]
-                    .xmin);
+  return __ldg(&reinterpret_cast<const StageTab*>(a.tabs)[(size_t)tile * nstages + stage].xmin);
 }
 
 // Issue of one stage by one thread: one tensor copy of the stage's 16 rows (segments
@@ -206,7 +207,8 @@ __device__ __forceinline__ int32_t stage_xmin(const TiledArgs& a, int stage, int
 template <typename T>
 __device__ __forceinline__ void issue_stage(const TiledArgs& a, int stage, int nstages,
                                             T* raw_buf, StageTab* tab_buf,
-                                            unsigned long long* bar, int32_t xmin, int64_t j0) {
+                                            unsigned long long* bar, int32_t xmin, int64_t j0,
+                                            int tile) {
   const uint32_t row_bytes = (uint32_t)a.row_slot * (uint32_t)sizeof(T);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_arrive_expect_tx(bar, kRows * row_bytes + (uint32_t)sizeof(StageTab));
@@ -217,7 +219,7 @@ __device__ __forceinline__ void issue_stage(const TiledArgs& a, int stage, int n
       "l"(reinterpret_cast<uint64_t>(&a.rows)), "r"(0), "r"(seg), "r"(stage * kRows),
       "r"(smem_addr(bar))
       : "memory");
-  bulk_g2s(tab_buf, a.tabs + ((size_t)blockIdx.x * nstages + stage) * sizeof(StageTab),
+  bulk_g2s(tab_buf, a.tabs + ((size_t)tile * nstages + stage) * sizeof(StageTab),
            (uint32_t)sizeof(StageTab), bar);
 }
 
@@ -234,12 +236,12 @@ struct AddrInputs {
 };
 
 __device__ __forceinline__ AddrInputs addr_inputs(const TiledArgs& a, int stage, int nstages,
-                                                  int ngroups, int trial0, int e) {
+                                                  int ngroups, int trial0, int e, int tile) {
   AddrInputs in{0, 0, 0, 0};
   const int gl = e / (kMaxCls * kG), p = (e / kG) % kMaxCls, k = e % kG;
   if (stage < nstages && stage * kNG + gl < ngroups) {
     const StageTab* st =
-        &reinterpret_cast<const StageTab*>(a.tabs)[(size_t)blockIdx.x * nstages + stage];
+        &reinterpret_cast<const StageTab*>(a.tabs)[(size_t)tile * nstages + stage];
     const GroupTab* gt = &st->g[gl];
     in.xmin = __ldg(&st->xmin);
     in.ncls = __ldg(&gt->ncls);
@@ -401,15 +403,17 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
   }
 }
 
+// One tile (trial tile bx, time tile by) of one range, by the whole CTA. Returns false when a
+// bounded wait ran out (the error bit is set and the tile's copies have landed); `reuse` = the
+// CTA has run tiles before, whose mbarriers are invalidated before they are initialised again.
 template <typename T, int TT, int NS, int D, int NT>
-__global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
-    k_dedisp_tiled(const __grid_constant__ TiledArgs a) {
+__device__ __forceinline__ bool tile_body(const TiledArgs& a, int bx, int by,
+                                          unsigned char* smem, bool reuse) {
   constexpr int KT = TT / 32;       // outputs per lane and trial
   constexpr int KP = TT / 64;       // pair words per lane and trial
   constexpr int W = NT / 32;        // warps
   constexpr int kTPW = D / W;       // trials per warp
   constexpr int HALVES = W / kWarps;  // warps sharing a build work list
-  extern __shared__ __align__(1024) unsigned char smem[];  // tensor copies land 128-aligned
   const SmemLayout SL = smem_layout(sizeof(T), 4, a.row_slot, a.zcap, NS);
   T* raw = reinterpret_cast<T*>(smem + SL.raw);
   uint32_t* Zbuf = reinterpret_cast<uint32_t*>(smem + SL.z);
@@ -418,15 +422,19 @@ __global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + SL.mbar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int trial0 = blockIdx.x * D;
+  const int trial0 = bx * D;
   const int ntr = min(D, a.n_trials - trial0);
-  const int64_t j0 = (int64_t)blockIdx.y * TT;
+  const int64_t j0 = (int64_t)by * TT;
   const int ngroups = a.cpad / kG;
   const int nstages = (ngroups + kNG - 1) / kNG;
   const size_t stage_elems = (size_t)kRows * a.row_slot;
 
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&mbar[s], 1);
+    for (int s = 0; s < NS; ++s) {
+      if (reuse) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&mbar[s]))
+                              : "memory");
+      mbar_init(&mbar[s], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -436,10 +444,11 @@ __global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
   {
     const int s0 = tid / kAddrEntries;
     if (s0 < 2) {
-      const AddrInputs in0 = addr_inputs(a, s0, nstages, ngroups, trial0, tid % kAddrEntries);
+      const AddrInputs in0 =
+          addr_inputs(a, s0, nstages, ngroups, trial0, tid % kAddrEntries, bx);
       addr_entry<T>(a, in0, j0, tid % kAddrEntries, &atab[s0]);
     }
-    if (tid < kAddrEntries) ain = addr_inputs(a, 2, nstages, ngroups, trial0, tid);
+    if (tid < kAddrEntries) ain = addr_inputs(a, 2, nstages, ngroups, trial0, tid, bx);
   }
   __syncthreads();
   // stages whose copies have been issued: NS in the prologue, then one per iteration s >= 1
@@ -449,8 +458,8 @@ __global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
   if (tid == NT - 32) {
     for (int s = 0; s < NS && s < nstages; ++s)
       issue_stage<T>(a, s, nstages, raw + (size_t)s * stage_elems, &tab[s], &mbar[s],
-                     stage_xmin(a, s, nstages), j0);
-    xmin_next = stage_xmin(a, NS, nstages);
+                     stage_xmin(a, s, nstages, bx), j0, bx);
+    xmin_next = stage_xmin(a, NS, nstages, bx);
   }
   bool ok0 = mbar_wait_bounded(&mbar[0], 0);
   if (ok0) build_stage<T, HALVES>(tab[0], atab[0], smem_addr(raw), Zbuf, warp % kWarps, lane,
@@ -473,15 +482,15 @@ __global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
       const int b2 = s2 % NS;
       if (tid == NT - 32) {
         issue_stage<T>(a, s2, nstages, raw + (size_t)b2 * stage_elems, &tab[b2], &mbar[b2],
-                       xmin_next, j0);
-        xmin_next = stage_xmin(a, s2 + 1, nstages);
+                       xmin_next, j0, bx);
+        xmin_next = stage_xmin(a, s2 + 1, nstages, bx);
       }
       issued = s2 + 1;
     }
     // row addressing of stage s + 2, into the buffer stage s used (read during iteration s - 1)
     if (tid < kAddrEntries) {
       if (s + 2 < nstages) addr_entry<T>(a, ain, j0, tid, &atab[s & 1]);
-      ain = addr_inputs(a, s + 3, nstages, ngroups, trial0, tid);
+      ain = addr_inputs(a, s + 3, nstages, ngroups, trial0, tid, bx);
     }
     // (2) pair words of stage s + 1
     bool ok = true;
@@ -532,7 +541,7 @@ __global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
       for (int s = s_abort; s < issued; ++s)
         mbar_wait_bounded(&mbar[s % NS], (uint32_t)((s / NS) & 1));
     }
-    return;
+    return false;
   }
 
   // ---- epilogue: series + exact moments
@@ -577,6 +586,50 @@ __global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
         atomicAdd(&m->s2hi, hi + ((old + lo < old) ? 1ull : 0ull));
       }
     }
+  }
+  return true;
+}
+
+// One launch per range: CTA (x, y) runs trial tile x, time tile y.
+template <typename T, int TT, int NS, int D, int NT>
+__global__ void __launch_bounds__(NT, tile_ctas(D, TT, NT))
+    k_dedisp_tiled(const __grid_constant__ TiledArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];  // tensor copies land 128-aligned
+  tile_body<T, TT, NS, D, NT>(a, blockIdx.x, blockIdx.y, smem, false);
+}
+
+// Persistent form: one CTA per SM takes tiles from a device work list that spans many ranges of
+// many plans (beams), until the list is exhausted. Segment k of the list holds every tile of
+// descriptor seg_desc[k] (trial tiles fastest, as the per-range grid orders them), items
+// seg_first[k] .. seg_first[k + 1] - 1. The shared-memory arrangement of each tile follows its
+// own descriptor; the launch provides the largest any descriptor needs.
+template <typename T, int TT, int NS, int D, int NT>
+__global__ void __launch_bounds__(NT, 1) k_dedisp_persistent(const __grid_constant__ PersistArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ long long item_s;
+  const int64_t total = p.seg_first[p.nseg];
+  bool reuse = false;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(p.counter, 1ull);
+    __syncthreads();
+    const int64_t item = item_s;
+    if (item >= total) break;  // uniform
+    int lo = 0, hi = p.nseg - 1;  // the segment holding the item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (p.seg_first[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const TiledArgs& a = p.descs[p.seg_desc[lo]];
+    // the tensor map was written to global memory by a copy: acquire it for the tensor proxy
+    // before the tile's first copy uses it
+    if (threadIdx.x == NT - 32)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&a.rows)
+                   : "memory");
+    const int64_t local = item - p.seg_first[lo];
+    const int ntx = (a.n_trials + D - 1) / D;
+    if (!tile_body<T, TT, NS, D, NT>(a, (int)(local % ntx), (int)(local / ntx), smem, reuse))
+      break;  // a bounded wait ran out (uniform): the error bit is set
+    reuse = true;
   }
 }
 
@@ -831,6 +884,11 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
   X(T, U16, 512, 3, 64, 1024) X(T, U16, 256, 4, 64, 512) X(T, U16, 256, 3, 64, 512) \
   X(T, U16, 256, 4, 32, 512) X(T, U16, 256, 3, 32, 512)
 #define DD_TILED_INSTANCES(X) DD_TILED_SHAPES(X, uint8_t, 0) DD_TILED_SHAPES(X, uint16_t, 1)
+// The persistent form exists for the 64 x 512 tile with 16 warps (the shape every plan measured
+// so far runs fastest on).
+#define DD_PERSIST_INSTANCES(X)                                                   \
+  X(uint8_t, 0, 512, 4, 64, 512) X(uint8_t, 0, 512, 3, 64, 512)                   \
+  X(uint16_t, 1, 512, 4, 64, 512) X(uint16_t, 1, 512, 3, 64, 512)
 
 // Host: plan one range and verify the tables against the delay table they were built from,
 // independently of how they were built. Returns the number of violations of:
@@ -918,6 +976,27 @@ int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, 
     }
   }
   return bad;
+}
+
+size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap, int nstage) {
+  return smem_layout(is_u16 ? 2 : 1, 4, row_slot, zcap, nstage).total;
+}
+
+cudaError_t launch_tiled_persistent(const PersistArgs& p, int is_u16, int tt, int nstage, int D,
+                                    int nt, size_t smem, int ctas, cudaStream_t st) {
+  if (p.nseg <= 0 || ctas <= 0) return cudaSuccess;
+#define DD_PERSIST(T, U16, TT, NS, DT, NTH)                                     \
+  if (is_u16 == U16 && tt == TT && nstage == NS && D == DT && nt == NTH) {       \
+    cudaError_t e = cudaFuncSetAttribute(k_dedisp_persistent<T, TT, NS, DT, NTH>, \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                            \
+    if (e != cudaSuccess) return e;                                             \
+    k_dedisp_persistent<T, TT, NS, DT, NTH><<<ctas, NTH, smem, st>>>(p);        \
+    return cudaGetLastError();                                                  \
+  }
+  DD_PERSIST_INSTANCES(DD_PERSIST)
+#undef DD_PERSIST
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t prepare_tiled(int is_u16, int tt, int nstage, int D, int nt, size_t smem) {

@@ -103,6 +103,18 @@ struct TiledArgs {
   CUtensorMap rows;        // the ring as [Cp][xd_stride / seg][seg] (make_ring_map)
 };
 
+// Arguments of the persistent tiled kernel: a device work list over many ranges (of many plans)
+// of one instance (data type, tile shape, staging buffers). Segment k covers every tile of
+// descs[seg_desc[k]]: items seg_first[k] .. seg_first[k + 1] - 1 (trial tiles fastest).
+struct PersistArgs {
+  const TiledArgs* descs;      // device [ndesc], 64-byte aligned (tensor maps inside)
+  const int32_t* seg_desc;     // device [nseg]
+  const int64_t* seg_first;    // device [nseg + 1]
+  int32_t nseg;
+  int32_t pad;
+  unsigned long long* counter; // device, zeroed before the launch
+};
+
 // Plan of the tiled kernel for one range (host): tile shape, shared-memory sizes and the
 // delay-class tables the kernel copies in per stage. ok = false: the range does not fit.
 struct TiledPlan {
@@ -136,6 +148,12 @@ cudaError_t prepare_tiled(int is_u16, int tt, int nstage, int trials, int thread
 cudaError_t launch_wait_selftest(int32_t* err, cudaStream_t st);
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, int trials, int threads,
                          cudaStream_t st);
+// The persistent form over a work list; smem = the largest staging arrangement of its
+// descriptors (smem_bytes), grid = ctas (one per SM).
+cudaError_t launch_tiled_persistent(const PersistArgs& p, int is_u16, int tt, int nstage,
+                                    int trials, int threads, size_t smem, int ctas,
+                                    cudaStream_t st);
+size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap, int nstage);
 
 // Tensor map of a channel-major ring (uint8, or uint16 when is_u16) for the tiled kernel's
 // stage copies: dims {128-byte segment, segments per row, cpad rows}, box {segment, nseg, 16}.
@@ -164,6 +182,17 @@ int sps_enqueue(dd_plan_s* plan, const int32_t* widths, int32_t nwidths, float t
 int plan_autotune(dd_plan_s* plan);
 int range_tile(dd_plan_s* plan, int r);
 void plan_redirect_errors(dd_plan_s* plan, int32_t* err);
+// A tiled dedispersion launch handed back by run_deferred for a persistent launch.
+struct DeferredTile {
+  TiledArgs args;
+  int32_t is_u16;
+  int32_t nstage;
+  size_t smem;
+};
+// dd_run on stream `st`, except that the range launches of the 64 x 512 x 512 tile shape are
+// appended to *out instead of being made (every other launch is made as dd_run makes it).
+int run_deferred(dd_plan_s* plan, const uint8_t* chunk, int64_t nsamp, cudaStream_t st,
+                 std::vector<DeferredTile>* out);
 // Serving support: make the next dd_run's dedispersion wait (once) for an event of another
 // plan on the same device; the event recorded when chunk `seq` of a plan has been searched
 // (nullptr if that chunk is not a searched chunk still held by the plan).

@@ -53,7 +53,7 @@ def _alone(w, x):
     return res
 
 
-@pytest.mark.parametrize("mode", ["direct", "graph", "autotune"])
+@pytest.mark.parametrize("mode", ["direct", "graph", "autotune", "persistent"])
 def test_batch_equals_each_beam_alone(mode):
     dd.build()
     beams = _beams()
@@ -62,7 +62,8 @@ def test_batch_equals_each_beam_alone(mode):
     dev = [torch.from_numpy(x).cuda() for _, x in beams]
     b = dd.Batch([(w.freqs(), w.tsamp, d) for (w, _), d in zip(beams, dev)],
                  w0.ranges_array(), 4096, w0.widths, w0.threshold, n_streams=2,
-                 graph=mode == "graph", autotune=mode == "autotune")
+                 graph=mode == "graph", autotune=mode == "autotune",
+                 persistent=mode == "persistent")
     try:
         matched = 0
         for step in range(2):  # a second step (graph replay) gives the same results
@@ -93,15 +94,18 @@ def test_device_input_plans_refuse_host_chunks():
         plan.close()
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batch_of_tiled_beams(graph):
+@pytest.mark.parametrize("graph,persistent", [(False, False), (True, False), (False, True),
+                                              (True, True)])
+def test_batch_of_tiled_beams(graph, persistent):
     """Beams of 256 fine channels whose ranges (x1, x2) run on the tiled kernel, whose error
     bits a batch collects in a word of its own: the step reports that word clean, and every
-    (beam, chunk) has exactly the candidates of the beam alone."""
+    (beam, chunk) has exactly the candidates of the beam alone -- also when each round's tiles
+    of every beam and range are taken from one work list by a persistent launch, directly and
+    as a replayed graph."""
     dd.build()
     ranges = (configs.DMRange(0.0, 0.0625, 70, 1), configs.DMRange(4.375, 0.125, 40, 2))
     beams = []
-    for k, nsamp in enumerate((12288, 8192)):
+    for k, nsamp in enumerate((12288, 8192, 6144)):
         w = configs.mid(nsamp=nsamp, chunk_len=4096, n_streams=1, npulses=3, nchans=4096,
                         ranges=ranges, index=40 + k)
         w.nchans, w.foff = 256, -300.0 / 1024
@@ -114,7 +118,8 @@ def test_batch_of_tiled_beams(graph):
     w0 = beams[0][0]
     dev = [torch.from_numpy(x).cuda() for _, x in beams]
     b = dd.Batch([(w.freqs(), w.tsamp, d) for (w, _), d in zip(beams, dev)],
-                 w0.ranges_array(), 4096, w0.widths, w0.threshold, n_streams=2, graph=graph)
+                 w0.ranges_array(), 4096, w0.widths, w0.threshold, n_streams=2, graph=graph,
+                 persistent=persistent)
     try:
         matched = 0
         for step in range(2):
