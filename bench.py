@@ -41,8 +41,8 @@ from synth import configs  # noqa: E402
 
 METRIC = "DM-trial·samples/s dedispersed"
 UNIT = "DM-trial·samples/s"
-# DRAM bytes per output sample of the dedispersion launches, from one ncu capture; valid only
-# for the kernel source it was taken on (its SHA-256 is stored beside the figure)
+# DRAM bytes over algorithmic bytes of the dedispersion launches, from one ncu capture; valid only
+# for the kernel source it was taken on (its SHA-256 is stored beside the figures)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dedisp_dram_traffic.json")
 DEDISP_SOURCE = os.path.join(ROOT, "paper_2101_00941_gb300", "csrc", "dd_dedisp.cu")
 
@@ -522,6 +522,62 @@ def transfer_workload(args):
     return 0
 
 
+def shapes_workload(args):
+    """Every tile shape of the tiled dedispersion kernel (forced by the plan's testing flags) and
+    the autotuned plan, on the 4096-channel and the out-of-core plans: each range's launch over a
+    full chunk window alone on one stream (best of three), in ms."""
+    import torch
+
+    import paper_2101_00941_gb300 as dd
+    torch.cuda.set_device(0)
+    dd.build()
+    shapes = (("64x512x512", 0), ("64x512x1024", dd.DD_FLAG_WARPS32),
+              ("64x256x512", dd.DD_FLAG_TILE256),
+              ("32x256x512", dd.DD_FLAG_TILE256 | dd.DD_FLAG_TRIALS32),
+              ("autotune", dd.DD_FLAG_AUTOTUNE))
+    res = {}
+    for name in ("mid", "ooc"):
+        w, _ = stream_workload(name, streams=1)
+        L = w.chunk_len
+        x = torch.empty((2, L, w.nchans), dtype=torch.uint8)
+        off = pulse_offsets(w)
+        for k in range(2):
+            w.generate(off, t0=k * L, nsamp=L, out=x[k].numpy())
+        xd = x.cuda()
+        st = torch.cuda.Stream()
+        for label, fl in shapes:
+            plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=1,
+                           max_width=max(w.widths),
+                           flags=fl | dd.DD_FLAG_TIMING | dd.DD_FLAG_DEVICE_INPUT)
+            chosen = []
+            for r in range(len(w.ranges)):
+                m = plan.model(r, 1)
+                chosen.append([m["tile_trials"], m["tile_samples"], m["cta_threads"]]
+                              if m["kind"] == dd.DD_KERNEL_TILED else "direct")
+            plan.run(xd[0], L, cuda_stream=st.cuda_stream)
+            plan.search(w.widths, w.threshold)
+            plan.sync()
+            best = None
+            for rep in range(3):
+                plan.stats(reset=True)
+                plan.run(xd[1], L, cuda_stream=st.cuda_stream)
+                plan.search(w.widths, w.threshold)
+                plan.sync()
+                ms = [plan.stats_range(r)[0] for r in range(len(w.ranges))]
+                best = ms if best is None else [min(a, b) for a, b in zip(best, ms)]
+            plan.close()
+            res[f"{w.name}/{label}"] = {"tiles": chosen, "ms": [round(v, 3) for v in best],
+                                         "total_ms": round(sum(best), 3)}
+        del xd
+    line = {"metric": "dedispersion ms per chunk window and range, by tile shape",
+            "value": res[next(k for k in res if k.endswith("/autotune"))]["total_ms"],
+            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "vs_baseline": None,
+            "dtype": "u8/i32", "data": "synthetic", "config": {"workload": "shapes"},
+            "shapes": res}
+    print(json.dumps(line))
+    return 0
+
+
 def peaks_workload(args):
     """The measured integer and shared-memory issue rates (dd_measure_peaks), three runs."""
     import torch
@@ -574,9 +630,10 @@ def launch_model(plan, w, O: int, T0: int, sizes):
     return tot, per
 
 
-def dram_traffic_per_output(w):
-    """DRAM bytes per output sample of the dedispersion launches from the committed capture, or
-    None when the capture was taken on another workload or another revision of the kernel."""
+def dram_traffic_ratio():
+    """DRAM bytes (read + write) of the dedispersion launches over their algorithmic bytes, from
+    the committed ncu capture, or None when the capture was taken on another revision of the
+    kernel source (its SHA-256 is stored beside the figures)."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)
@@ -586,8 +643,7 @@ def dram_traffic_per_output(w):
         return None
     if rec.get("kernel_source_sha256") != sha:
         return None
-    ent = rec.get("workloads", {}).get(w.name.rsplit("_", 1)[0])
-    return None if ent is None else float(ent["dram_bytes"]) / float(ent["outputs"])
+    return float(rec["dram_bytes"]) / float(rec["algorithmic_bytes"])
 
 
 def main(args):
@@ -664,7 +720,7 @@ def main(args):
     dd_s = dd_ms * 1e-3
     achieved = tot["adds"] / dd_s if dd_s > 0 else None
     smem_wf = tot["smem_wavefronts"] + tot["copy_bytes"] / 128.0
-    bpo = dram_traffic_per_output(w)
+    ratio = dram_traffic_ratio()
     per_range = []
     for r, (rms, rn) in enumerate(range_ms):
         p = per_solo[r]
@@ -708,8 +764,14 @@ def main(args):
         "roofline": {
             "bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "adds/s",
             "frac": achieved / peak_int if achieved else None,
-            "traffic": bpo * tot["outputs"] / dd_n if (bpo and dd_n) else None,
-            "traffic_unit": "bytes per launch", "kernel": "k_dedisp_tiled (all ranges)",
+            "traffic": ratio * tot["dram_bytes"] / dd_n if (ratio and dd_n) else None,
+            "traffic_unit": "bytes per launch",
+            "traffic_note": "measured DRAM bytes / algorithmic bytes of a committed ncu capture "
+                            "of the same kernel source (profiles/dedisp_dram_traffic.json) x the "
+                            "algorithmic bytes of the timed launches (dd_plan_model); null when "
+                            "the kernel source has changed since the capture",
+            "algorithmic_dram_bytes_per_launch": tot["dram_bytes"] / dd_n if dd_n else None,
+            "kernel": "k_dedisp_tiled (all ranges)",
             "launches_timed": dd_n, "dedisp_ms": dd_ms,
             "peak_note": "measured: integer lane-instructions per SM-clock with LOP3 and DP2A "
                          "interleaved (dd_measure_peaks) x SMs x median SM clock of the timed "
@@ -749,7 +811,8 @@ if __name__ == "__main__":
                     help="samples per beam (a multiple of the chunk length; smaller only for "
                          "tests and profiler captures)")
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the chunks rotate over")
-    ap.add_argument("--workload", choices=["ooc", "mid", "serve", "batch", "transfer", "peaks"],
+    ap.add_argument("--workload", choices=["ooc", "mid", "serve", "batch", "transfer", "peaks",
+                                           "shapes"],
                     default="ooc")
     ap.add_argument("--batch-scale", type=int, default=1,
                     help="batch: divide every beam's length by this (profiling only)")
@@ -770,4 +833,6 @@ if __name__ == "__main__":
         sys.exit(transfer_workload(a))
     if a.workload == "peaks":
         sys.exit(peaks_workload(a))
+    if a.workload == "shapes":
+        sys.exit(shapes_workload(a))
     sys.exit(batch_workload(a) if a.workload == "batch" else main(a))
