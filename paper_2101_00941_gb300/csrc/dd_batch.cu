@@ -181,23 +181,26 @@ int enqueue_step_persistent(dd_batch_s* b) {
         fpos += in.nseg + 1;
         insts.push_back(in);
       }
-    if (defs.empty()) continue;
     ddk::TiledArgs* dd_ = b->d_descs + c * b->max_descs;
     int32_t* ds = b->d_segd + c * b->max_descs;
     int64_t* df = b->d_segf + c * (b->max_descs + 4);
-    rc = ck(cudaMemcpyAsync(dd_, hd, sizeof(ddk::TiledArgs) * defs.size(), cudaMemcpyHostToDevice,
-                            b->root),
-            "work list");
-    if (rc == DD_OK)
-      rc = ck(cudaMemcpyAsync(ds, hs, sizeof(int32_t) * nseg_total, cudaMemcpyHostToDevice,
-                              b->root),
+    // (a round whose ranges all run on the direct kernel has no work list, only searches)
+    if (!defs.empty()) {
+      rc = ck(cudaMemcpyAsync(dd_, hd, sizeof(ddk::TiledArgs) * defs.size(),
+                              cudaMemcpyHostToDevice, b->root),
               "work list");
-    if (rc == DD_OK)
-      rc = ck(cudaMemcpyAsync(df, hf, sizeof(int64_t) * fpos, cudaMemcpyHostToDevice, b->root),
-              "work list");
-    if (rc == DD_OK)
-      rc = ck(cudaMemsetAsync(b->d_counters + 4 * c, 0, 4 * sizeof(unsigned long long), b->root),
-              "counters");
+      if (rc == DD_OK)
+        rc = ck(cudaMemcpyAsync(ds, hs, sizeof(int32_t) * nseg_total, cudaMemcpyHostToDevice,
+                                b->root),
+                "work list");
+      if (rc == DD_OK)
+        rc = ck(cudaMemcpyAsync(df, hf, sizeof(int64_t) * fpos, cudaMemcpyHostToDevice, b->root),
+                "work list");
+      if (rc == DD_OK)
+        rc = ck(cudaMemsetAsync(b->d_counters + 4 * c, 0, 4 * sizeof(unsigned long long),
+                                b->root),
+                "counters");
+    }
     for (size_t g = 0; rc == DD_OK && g < insts.size(); ++g) {
       const Inst& in = insts[g];
       ddk::PersistArgs pa;
