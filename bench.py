@@ -680,7 +680,7 @@ def main(args):
     t_plan = time.perf_counter()
     plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=w.n_streams,
                    max_width=max(w.widths), peak_block=32, device=dev,
-                   flags=dd.DD_FLAG_TIMING | dd.DD_FLAG_AUTOTUNE)
+                   flags=dd.DD_FLAG_TIMING | (0 if args.no_autotune else dd.DD_FLAG_AUTOTUNE))
     t_plan = time.perf_counter() - t_plan
     O = plan.O
     shapes = [plan.model(r, 1) for r in range(len(w.ranges))]
@@ -807,6 +807,8 @@ if __name__ == "__main__":
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plan without timing the tile shapes (profiler captures count launches)")
     ap.add_argument("--nsamp", type=int, default=None,
                     help="samples per beam (a multiple of the chunk length; smaller only for "
                          "tests and profiler captures)")

@@ -282,20 +282,24 @@ __device__ __forceinline__ void row_words(const RowItem& it, int k, uint32_t& w0
   w1 = lds<OFF + 4>(it.addr[k]);
 }
 
-// uint8 data. A lane builds units u and u + 32; unit u covers pair words 4u .. 4u + 3, i.e.
-// the eight-channel sums S[4u .. 4u + 4] (one more than its words, which the last pair word
-// needs). Each channel's two row words are funnel-shifted to the class's first sample; bytes
-// are split into even/odd 16-bit lanes so that eight channels add without carries (8 x 255 <
-// 2^16), and the fifth sample, byte (shift / 8) of the second row word, is added by a DP4A on
-// the rotated word. The pair words go to the class's even plane (4u, 4u + 2) and odd plane
-// (4u + 1, 4u + 3); lanes take consecutive units, so every load and store is free of bank
-// conflicts.
+// uint8 data. Unit u covers pair words 4u .. 4u + 3, i.e. the eight-channel sums
+// S[4u .. 4u + 4] (one more than its words, which the last pair word needs). Each channel's two
+// row words are funnel-shifted to the class's first sample; bytes are split into even/odd
+// 16-bit lanes so that eight channels add without carries (8 x 255 < 2^16). The fifth sum is
+// the next unit's first one, S[4(u + 1)]: the next lane's, taken with one shuffle. So a block of
+// 32 lanes stores 31 units (lanes 0 .. 30); lane 31 computes the next block's first unit only
+// to hand its first sum to lane 30 (kBlock = 31). The pair words go to the class's even plane
+// (4u, 4u + 2) and odd plane (4u + 1, 4u + 3); lanes take consecutive units, so every load and
+// store is free of bank conflicts. Every lane of the warp runs the unit (the shuffle needs them
+// all); `live` says whether this lane's words are stored.
 template <>
 struct Word<uint8_t> {
-  static constexpr int kUnit = 4;  // pair words per unit
+  static constexpr int kUnit = 4;   // pair words per unit
+  static constexpr int kBlock = 31; // units stored per 32-lane block
   template <int OFF>
-  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* ev, uint32_t* od) {
-    uint32_t e = 0, o = 0, s4 = 0;
+  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* ev, uint32_t* od,
+                                              bool live) {
+    uint32_t e = 0, o = 0;
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
       uint32_t w0, w1;
@@ -303,15 +307,17 @@ struct Word<uint8_t> {
       const uint32_t a = __funnelshift_r(w0, w1, it.sh[k]);  // samples 0..3 in bytes 0..3
       e += a & 0x00FF00FFu;                                  // samples 0, 2
       o += __byte_perm(a, 0, 0x4341);                        // samples 1, 3
-      s4 = __dp4a(__funnelshift_r(w1, w1, it.sh[k]), 1u, s4);  // sample 4
     }
-    uint2 x, y;
-    x.x = __byte_perm(e, o, 0x5410);   // S0 | S1 << 16
-    x.y = __byte_perm(e, o, 0x7632);   // S2 | S3 << 16
-    y.x = __byte_perm(o, e, 0x7610);   // S1 | S2 << 16
-    y.y = __byte_perm(o, s4, 0x5432);  // S3 | S4 << 16
-    *reinterpret_cast<uint2*>(ev) = x;
-    *reinterpret_cast<uint2*>(od) = y;
+    const uint32_t nx = __shfl_down_sync(0xffffffffu, e, 1);  // low half: S4 (next unit's S0)
+    if (live) {
+      uint2 x, y;
+      x.x = __byte_perm(e, o, 0x5410);   // S0 | S1 << 16
+      x.y = __byte_perm(e, o, 0x7632);   // S2 | S3 << 16
+      y.x = __byte_perm(o, e, 0x7610);   // S1 | S2 << 16
+      y.y = __byte_perm(o, nx, 0x5432);  // S3 | S4 << 16
+      *reinterpret_cast<uint2*>(ev) = x;
+      *reinterpret_cast<uint2*>(od) = y;
+    }
   }
 };
 
@@ -322,8 +328,10 @@ struct Word<uint8_t> {
 template <>
 struct Word<uint16_t> {
   static constexpr int kUnit = 2;
+  static constexpr int kBlock = 32;  // units per 32-lane block
   template <int OFF>
-  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* ev, uint32_t* od) {
+  static __device__ __forceinline__ void unit(const RowItem& it, uint32_t* ev, uint32_t* od,
+                                              bool /*live: always, lanes past the class skip*/) {
     uint32_t e = 0, s2 = 0;
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
@@ -358,7 +366,8 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
     const int gi = (int)((wk >> 4) & 1), p = (int)(wk & 15);
     const int b0 = (int)((wk >> 8) & 255), nb = (int)(wk >> 16);
     const int zlen = tb.g[gi].cls[p].zlen;
-    int u = 32 * (b0 + (HALVES == 2 ? half : 0)) + lane;
+    constexpr int B = Word<T>::kBlock;  // units per block
+    int u = B * (b0 + (HALVES == 2 ? half : 0)) + lane;
     const uint4 ad = at.addr[gi][p];
     const uint2 sv = at.sh[gi][p];
     const uint32_t base = rawb + 4u * (uint32_t)u;  // one row word per unit
@@ -379,33 +388,60 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
     // even plane: pair words 0, 2, 4, ... of the class; odd plane: 1, 3, 5, ...
     uint32_t* ev = Zs + tb.g[gi].cls[p].zoff + (U / 2) * u;
     uint32_t* od = ev + zlen / 2;
-    if (HALVES == 1) {
-      for (int b = 0; b < nb; b += 2) {
-        if (u * U < zlen) Word<T>::template unit<0>(it, ev, od);
-        if (b + 1 < nb && (u + 32) * U < zlen)
-          Word<T>::template unit<128>(it, ev + 16 * U, od + 16 * U);
+    if constexpr (B == 31) {
+      // uint8: every lane runs every unit (shuffles); lanes 0 .. 30 store the block's units.
+      // Lanes past the class compute nothing they store; their loads stay inside the CTA's
+      // shared memory (the staged rows are followed by the word planes).
+      const bool store_lane = lane < 31;
+      if (HALVES == 1) {
+        for (int b = 0; b < nb; b += 2) {
+          Word<T>::template unit<0>(it, ev, od, store_lane && u * U < zlen);
+          if (b + 1 < nb)
+            Word<T>::template unit<4 * B>(it, ev + B * U / 2, od + B * U / 2,
+                                          store_lane && (u + B) * U < zlen);
 #pragma unroll
-        for (int k = 0; k < kG; ++k) it.addr[k] += 256u;  // 64 units further
-        u += 64;
-        ev += 32 * U;
-        od += 32 * U;
+          for (int k = 0; k < kG; ++k) it.addr[k] += 8u * B;  // two blocks further
+          u += 2 * B;
+          ev += B * U;
+          od += B * U;
+        }
+      } else {
+        for (int b = half; b < nb; b += 2) {
+          Word<T>::template unit<0>(it, ev, od, store_lane && u * U < zlen);
+#pragma unroll
+          for (int k = 0; k < kG; ++k) it.addr[k] += 8u * B;
+          u += 2 * B;
+          ev += B * U;
+          od += B * U;
+        }
       }
     } else {
-      for (int b = half; b < nb; b += 2) {
-        if (u * U < zlen) Word<T>::template unit<0>(it, ev, od);
+      // uint16: lanes past the class skip their units
+      if (HALVES == 1) {
+        for (int b = 0; b < nb; b += 2) {
+          if (u * U < zlen) Word<T>::template unit<0>(it, ev, od, true);
+          if (b + 1 < nb && (u + B) * U < zlen)
+            Word<T>::template unit<4 * B>(it, ev + B * U / 2, od + B * U / 2, true);
 #pragma unroll
-        for (int k = 0; k < kG; ++k) it.addr[k] += 256u;  // 64 units further
-        u += 64;
-        ev += 32 * U;
-        od += 32 * U;
+          for (int k = 0; k < kG; ++k) it.addr[k] += 8u * B;  // two blocks further
+          u += 2 * B;
+          ev += B * U;
+          od += B * U;
+        }
+      } else {
+        for (int b = half; b < nb; b += 2) {
+          if (u * U < zlen) Word<T>::template unit<0>(it, ev, od, true);
+#pragma unroll
+          for (int k = 0; k < kG; ++k) it.addr[k] += 8u * B;
+          u += 2 * B;
+          ev += B * U;
+          od += B * U;
+        }
       }
     }
   }
 }
 
-// One tile (trial tile bx, time tile by) of one range, by the whole CTA. Returns false when a
-// bounded wait ran out (the error bit is set and the tile's copies have landed); `reuse` = the
-// CTA has run tiles before, whose mbarriers are invalidated before they are initialised again.
 template <typename T, int TT, int NS, int D, int NT>
 __device__ __forceinline__ bool tile_body(const TiledArgs& a, int bx, int by,
                                           unsigned char* smem, bool reuse) {
@@ -665,18 +701,19 @@ cudaError_t prepare_t(size_t smem) {
 
 namespace {
 
-// Cut a stage's classes into blocks of 32 units (U pair words each) and deal them to the
-// warps in contiguous shares of ceil(blocks / warps); false if a share needs more ranges than
-// a warp's list holds or a class more blocks than a range can name.
-bool deal_work(StageTab& st, int U) {
+// Cut a stage's classes into blocks of B units (U pair words each; B = 31 for uint8 data, 32
+// for uint16: Word<T>::kBlock) and deal them to the warps in contiguous shares of
+// ceil(blocks / warps); false if a share needs more ranges than a warp's list holds or a class
+// more blocks than a range can name.
+bool deal_work(StageTab& st, int U, int B) {
   int total = 0;
   for (int gl = 0; gl < kNG; ++gl)
-    for (int p = 0; p < st.g[gl].ncls; ++p) total += (st.g[gl].cls[p].zlen / U + 31) / 32;
+    for (int p = 0; p < st.g[gl].ncls; ++p) total += (st.g[gl].cls[p].zlen / U + B - 1) / B;
   const int share = (total + kWarps - 1) / kWarps;
   int w = 0, used = 0;
   for (int gl = 0; gl < kNG; ++gl)
     for (int p = 0; p < st.g[gl].ncls; ++p) {
-      const int nb = (st.g[gl].cls[p].zlen / U + 31) / 32;
+      const int nb = (st.g[gl].cls[p].zlen / U + B - 1) / B;
       if (nb > 255) return false;
       int b = 0;
       while (b < nb) {
@@ -720,8 +757,9 @@ cudaError_t launch_wait_selftest(int32_t* err, cudaStream_t st) {
 //   accumulation : every warp loads, for its kTPW trials and TT / 64 pair-word columns, one word
 //                  per group present (trials past the range's end load too), plus the trials'
 //                  zstart entries;
-//   build        : per 32-unit block, 2 row words for each of the 8 channels and the two plane
-//                  stores; per work range, its descriptor, class entry and addressing words;
+//   build        : per block (31 units for uint8 data, 32 for uint16), 2 row words for each of
+//                  the 8 channels and the two plane stores; per work range, its descriptor,
+//                  class entry and addressing words;
 //   addressing   : two stores per (group, class, channel) entry, by the first 8 warps;
 //   copies       : the tensor copy of the 16 staged rows and the bulk copy of the stage table.
 static void tiled_smem_work(TiledPlan& P, int ntiles, int nstages, int ngroups, bool u16) {
@@ -845,7 +883,7 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
         }
         gt.ncls = ncls;
       }
-      if (!deal_work(st, U)) return P;
+      if (!deal_work(st, U, u16 ? 32 : 31)) return P;
       zcap = std::max<int64_t>(zcap, words);
     }
   }
@@ -898,14 +936,15 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
 //   - class word ranges start and end on 16-byte boundaries;
 //   - the stage's copy start is the smallest first-trial delay of its rows, and every read of
 //     every trial stays inside the staged row;
-//   - the build work lists cover every 32-unit block of every class exactly once.
+//   - the build work lists cover every block (31 units for uint8 data, 32 for uint16) of every
+//     class exactly once.
 int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, int tt, int D,
                          int* ok) {
   const TiledPlan P = tiled_plan(tab, ntr, cpad, decimation, tt, D, kThreads);
   *ok = P.ok ? 1 : 0;
   if (!P.ok) return 0;
   const bool u16 = decimation > 1;
-  const int U = u16 ? 2 : 4, SEG = kSegBytes / (u16 ? 2 : 1);
+  const int U = u16 ? 2 : 4, SEG = kSegBytes / (u16 ? 2 : 1), B = u16 ? 32 : 31;
   const int ngroups = cpad / kG, nstages = (ngroups + kNG - 1) / kNG;
   const int ntiles = (ntr + D - 1) / D;
   const StageTab* tabs = reinterpret_cast<const StageTab*>(P.tabs.data());
@@ -925,7 +964,7 @@ int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, 
       std::vector<int> first_block(kNG * kMaxCls + 1, 0);
       for (int gl = 0; gl < kNG; ++gl)
         for (int p = 0; p < kMaxCls; ++p) {
-          const int nb = p < st.g[gl].ncls ? (st.g[gl].cls[p].zlen / U + 31) / 32 : 0;
+          const int nb = p < st.g[gl].ncls ? (st.g[gl].cls[p].zlen / U + B - 1) / B : 0;
           first_block[gl * kMaxCls + p + 1] = first_block[gl * kMaxCls + p] + nb;
         }
       covered.assign(first_block.back(), 0);
