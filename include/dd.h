@@ -269,8 +269,10 @@ int sps_run_ex(dd_plan_t plan, const int32_t* widths, int32_t nwidths, float thr
  * Errors: DD_ERR_STATE (unknown, recycled or unsearched chunk), DD_ERR_TIMEOUT (the wait ran
  * out, or a dedispersion kernel of this chunk ran out of its bounded device-side wait, so the
  * chunk's results are not valid; later chunks are not affected), DD_ERR_CAP (more than cap or
- * than opts.max_cands; *ncands holds the true count, out holds the first cap found in sorted
- * order of those kept), DD_ERR_CUDA.
+ * than opts.max_cands; *ncands holds the true count, out holds the first cap in sorted order of
+ * those kept; when more than opts.max_cands were found, which ones the device buffer kept
+ * depends on the order the search's blocks ran in, so only the count is reproducible),
+ * DD_ERR_CUDA.
  */
 int dd_candidates(dd_plan_t plan, int64_t seq, dd_cand_t* out, int64_t cap, int64_t* ncands,
                   int64_t timeout_ms);
