@@ -681,6 +681,7 @@ def main(args):
     plan = dd.Plan(w.freqs(), w.tsamp, w.ranges_array(), L, n_streams=w.n_streams,
                    max_width=max(w.widths), peak_block=32, device=dev,
                    flags=dd.DD_FLAG_TIMING | (0 if args.no_autotune else dd.DD_FLAG_AUTOTUNE))
+    nfused = plan.fuse_search(w.widths) if args.fused else 0
     t_plan = time.perf_counter() - t_plan
     O = plan.O
     shapes = [plan.model(r, 1) for r in range(len(w.ranges))]
@@ -720,7 +721,7 @@ def main(args):
     dd_s = dd_ms * 1e-3
     achieved = tot["adds"] / dd_s if dd_s > 0 else None
     smem_wf = tot["smem_wavefronts"] + tot["copy_bytes"] / 128.0
-    ratio = dram_traffic_ratio()
+    ratio = None if nfused else dram_traffic_ratio()  # the record is of the plain kernel
     per_range = []
     for r, (rms, rn) in enumerate(range_ms):
         p = per_solo[r]
@@ -750,7 +751,8 @@ def main(args):
                    "chunk_len": L, "chunks": nchunks, "n_streams": w.n_streams,
                    "widths": list(w.widths), "threshold": w.threshold, "overlap": O,
                    "input": ring_note,
-                   "l2": f"every chunk {L * w.nchans / 1e9:.1f} GB > L2 (no flush)"},
+                   "l2": f"every chunk {L * w.nchans / 1e9:.1f} GB > L2 (no flush)",
+                   "fused_search_ranges": nfused},
         "real_time_factor": obs / (ms * 1e-3 / args.steps),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": w.nsamp * w.nchans,
                 "d2h_bytes_per_step": int(ncand_e2e / args.steps * 32 + nchunks * 16),
@@ -771,7 +773,8 @@ def main(args):
                             "algorithmic bytes of the timed launches (dd_plan_model); null when "
                             "the kernel source has changed since the capture",
             "algorithmic_dram_bytes_per_launch": tot["dram_bytes"] / dd_n if dd_n else None,
-            "kernel": "k_dedisp_tiled (all ranges)",
+            "kernel": ("k_dedisp_fused + k_fused_edges (the search's position pass fused; "
+                       f"{nfused} ranges)") if nfused else "k_dedisp_tiled (all ranges)",
             "launches_timed": dd_n, "dedisp_ms": dd_ms,
             "peak_note": "measured: integer lane-instructions per SM-clock with LOP3 and DP2A "
                          "interleaved (dd_measure_peaks) x SMs x median SM clock of the timed "
@@ -807,6 +810,9 @@ if __name__ == "__main__":
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused", action="store_true",
+                    help="ooc/mid: fuse the search's position pass into dedispersion "
+                         "(dd_fuse_search); the series are not written")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan without timing the tile shapes (profiler captures count launches)")
     ap.add_argument("--nsamp", type=int, default=None,

@@ -147,9 +147,11 @@ int dd_plan_kernel(dd_plan_t plan, int32_t range, int32_t* kind, int32_t* tile_s
  *   ctas_per_sm        : CTAs of the tiled kernel's tile shape per SM (1 or 2), else 0
  *   outputs            : DM-trial*samples, n_trials * nout
  *   adds               : algorithmic channel-adds of the brute-force sum (Sec. 2.1), outputs*nchans
+ *   fused              : 1 when the range's search is fused into the kernel (dd_fuse_search)
  *   dram_bytes         : algorithmic DRAM bytes: each channel's window of decimated input
  *                        (nout + the range's largest delay samples) read once, the int32 series
- *                        written once
+ *                        written once (fused: a 4-byte sum and a 1-byte sample per trial, width
+ *                        and peak block instead, plus the series if they are kept)
  *   smem_wavefronts    : tiled kernel only (else 0): warp-wide shared-memory accesses the launch
  *                        issues (one wavefront each: the kernel's accesses have no bank
  *                        conflicts), counted from the plan-time tables
@@ -163,7 +165,7 @@ typedef struct {
   int32_t tile_trials;
   int32_t cta_threads;
   int32_t ctas_per_sm;
-  int32_t pad;
+  int32_t fused;
   int64_t outputs;
   double adds;
   double dram_bytes;
@@ -198,6 +200,8 @@ int dd_run(dd_plan_t plan, const uint8_t* chunk, int64_t nsamp, void* cuda_strea
  *   len     : samples of the chunk window (row j = global decimated index *j0 + j)
  *   stride  : row stride in elements;  j0 : global decimated index of sample 0 (may be NULL)
  * The data is complete once the chunk's stream has finished (dd_sync or dd_candidates).
+ * Errors: DD_ERR_ARG, DD_ERR_STATE (no chunk has been run, or the range's search is fused and
+ * its series are not kept: dd_fuse_search).
  */
 int dd_series(dd_plan_t plan, int32_t range, const int32_t** dev_ptr, int64_t* len,
               int64_t* stride, int64_t* j0);
@@ -225,14 +229,44 @@ typedef struct {
 int dd_moments(dd_plan_t plan, int32_t range, const dd_moments_t** dev_ptr, int64_t* n);
 
 /*
+ * dd_fuse_search -- fuse the search's position pass into the dedispersion kernel (Sec. 2.1 sums
+ * followed by the Sec. 2.2 boxcars), so that the int32 series need not be written to HBM and
+ * read back. From the plan's first dd_run on, every range whose widths (those of `widths` that
+ * are multiples of its decimation d, divided by d) are all <= 512 and whose kernel is the tiled
+ * one is dedispersed by the fused form (re-planned on the 64-trial x 512-sample tile if the plan
+ * chose another shape): after each tile, per (trial, width, peak block) the block's largest
+ * boxcar sum and its earliest sample are recorded, boxcars reaching into the previous tile
+ * included. sps_run then turns the records into candidates with the window moments; they are
+ * the candidates the plain search finds (same statistics, evaluation order and tie rules).
+ *   widths, nwidths : the search's widths (original samples), as sps_run; every later sps_run
+ *                     on the plan must pass exactly these
+ *   fuse_flags      : 0 or DD_FUSE_KEEP_SERIES (fused ranges also write their series, for
+ *                     dd_series and the clipped estimator)
+ *   nfused          : receives the number of fused ranges (may be NULL); ranges not fused keep
+ *                     the plain path
+ * Call once, after dd_plan and before the first dd_run. It allocates the record buffers (per
+ * stream slot: 5 bytes per trial, width and peak block, plus the segment edges) and, without
+ * DD_FUSE_KEEP_SERIES, gives up the fused ranges' series buffers: dd_series on such a range
+ * returns DD_ERR_STATE, as does sps_run_ex with DD_EST_CLIPPED.
+ * Errors: DD_ERR_ARG (widths, flags), DD_ERR_STATE (a chunk was run, or called twice),
+ * DD_ERR_NOMEM, DD_ERR_CUDA; on an error the plan is unchanged.
+ */
+#define DD_FUSE_KEEP_SERIES 1u
+int dd_fuse_search(dd_plan_t plan, const int32_t* widths, int32_t nwidths, uint32_t fuse_flags,
+                   int32_t* nfused);
+
+/*
  * sps_run -- enqueue the single pulse search of the most recent chunk (Sec. 2.2).
  *   widths    : host [nwidths] boxcar widths in original samples, strictly increasing,
  *               1 <= w <= max_width. Range r searches the widths w with w >= d_r and
  *               w % d_r == 0, as w/d_r decimated samples.
  *   threshold : candidates have SNR >= threshold
  * Enqueued on the chunk's own stream after its dedispersion (stream-ordered; no cross-stream
- * wait on atomics). Asynchronous; collect the result with dd_candidates.
- * Errors: DD_ERR_ARG, DD_ERR_STATE (no chunk, or already searched), DD_ERR_CUDA.
+ * wait on atomics). Asynchronous; collect the result with dd_candidates. On a plan whose search
+ * is fused (dd_fuse_search) the widths must be the fused ones, and the fused ranges' candidates
+ * come from the block records of the dedispersion kernel.
+ * Errors: DD_ERR_ARG (also: other widths than a fused plan's), DD_ERR_STATE (no chunk, or
+ * already searched), DD_ERR_CUDA.
  */
 int sps_run(dd_plan_t plan, const int32_t* widths, int32_t nwidths, float threshold);
 

@@ -32,6 +32,7 @@ DD_FLAG_AUTOTUNE = 32
 DD_FLAG_WARPS32 = 64
 DD_EST_WINDOW = 0
 DD_EST_CLIPPED = 1
+DD_FUSE_KEEP_SERIES = 1
 DD_BATCH_GRAPH = 1
 DD_BATCH_AUTOTUNE = 2
 DD_BATCH_PERSISTENT = 4
@@ -61,7 +62,7 @@ class dd_opts_t(ctypes.Structure):
 class dd_launch_model_t(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("tile_samples", ctypes.c_int32),
                 ("tile_trials", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("fused", ctypes.c_int32),
                 ("outputs", ctypes.c_int64), ("adds", ctypes.c_double),
                 ("dram_bytes", ctypes.c_double), ("smem_wavefronts", ctypes.c_double),
                 ("copy_bytes", ctypes.c_double)]
@@ -127,6 +128,7 @@ def lib() -> ctypes.CDLL:
         L.dd_run.argtypes = [vp, vp, i64, vp]
         L.dd_series.argtypes = [vp, i32, P(vp), P(i64), P(i64), P(i64)]
         L.sps_run.argtypes = [vp, vp, i32, f32]
+        L.dd_fuse_search.argtypes = [vp, vp, i32, ctypes.c_uint32, P(i32)]
         L.sps_run_ex.argtypes = [vp, vp, i32, f32, P(dd_sps_opts_t)]
         L.dd_candidates.argtypes = [vp, i64, vp, i64, P(i64), i64]
         L.dd_sync.argtypes = [vp]
@@ -255,6 +257,16 @@ def dd_moments(plan: int, range_idx: int):
     p, n = ctypes.c_void_p(), ctypes.c_int64()
     _check(lib().dd_moments(plan, int(range_idx), ctypes.byref(p), ctypes.byref(n)))
     return p.value, n.value
+
+
+def dd_fuse_search(plan: int, widths, keep_series: bool = False) -> int:
+    """Fuse the search's position pass into the dedispersion kernel (see dd.h); returns the
+    number of fused ranges."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(lib().dd_fuse_search(plan, w.ctypes.data, int(w.size),
+                                DD_FUSE_KEEP_SERIES if keep_series else 0, ctypes.byref(n)))
+    return n.value
 
 
 def dd_plan_model(plan: int, range_idx: int, nout: int) -> dict:
@@ -390,6 +402,10 @@ class Plan:
 
     def model(self, range_idx, nout):
         return dd_plan_model(self.h, range_idx, nout)
+
+    def fuse_search(self, widths, keep_series=False) -> int:
+        """dd_fuse_search: returns the number of fused ranges."""
+        return dd_fuse_search(self.h, widths, keep_series)
 
     def sync(self):
         dd_sync(self.h)

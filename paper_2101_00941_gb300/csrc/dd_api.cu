@@ -152,6 +152,7 @@ struct Slot {
   cudaEvent_t ev_sps = nullptr;           // search + count readback done
   uint8_t* h_stage = nullptr;             // pinned staging buffer (staging_threads > 0)
   cudaEvent_t ev_staged = nullptr;        // copy out of h_stage finished
+  uint8_t* fused = nullptr;               // fused-search records of every fused range
   int64_t seq = -1, T = 0, n = 0, lo = 0, hi = 0;
   bool searched = false;
 };
@@ -175,6 +176,17 @@ struct RangeKernel {
   uint8_t* d_tabs = nullptr;  // device copy of the delay-class tables
   int64_t lsu_wavefronts = 0; // shared-memory work of one row of time tiles (TiledPlan)
   int64_t copy_bytes = 0;
+  // search fused into the kernel (dd_fuse_search): decimated widths, the largest (hist),
+  // shared-memory arrangement, most segments, and the offsets of the range's block records
+  // (keys, offsets) and segment edges in the slot's fused arena
+  bool fused = false;
+  int nw = 0;
+  int wd[ddk::kMaxWidths] = {};
+  int hist = 0, hp = 0;
+  int32_t e_off = 0;
+  size_t fsmem = 0;
+  int smax = 0;
+  size_t key_off = 0, off_off = 0, edge_off = 0;
 };
 
 struct dd_plan_s {
@@ -205,6 +217,9 @@ struct dd_plan_s {
   StagingPool* pool = nullptr;     // staging_threads > 0
   int32_t* err_word = nullptr;     // if set, kernel error bits go here instead of the slot's
   cudaEvent_t gate = nullptr;      // if set, the next chunk's dedispersion waits for it (once)
+  std::vector<int32_t> fused_widths;  // dd_fuse_search's widths (original samples); empty: none
+  bool fused_series = false;       // fused ranges also write their series
+  int sms = 0;
   // dedispersion timing (DD_FLAG_TIMING): every launch is bracketed by an event pair; the pairs
   // are turned into [start, end) intervals against a common reference event and merged, so that
   // launches of different chunks running at the same time on different streams count once
@@ -236,6 +251,7 @@ void free_plan(dd_plan_s* p) {
     cudaFree(s.ring1);
     for (auto* r : s.ringd) cudaFree(r);
     cudaFree(s.series);
+    cudaFree(s.fused);
     cudaFree(s.mom);
     cudaFree(s.wst);
     cudaFree(s.cands);
@@ -395,6 +411,8 @@ int sps_enqueue(dd_plan_s* p, const int32_t* widths, int32_t nwidths, float thre
   if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
   Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
   if (s.searched) return fail(DD_ERR_STATE, "the latest chunk was already searched");
+  for (const auto& k : p->rk)
+    if (k.fused) return fail(DD_ERR_STATE, "a fused plan's search runs through sps_run");
   cudaStream_t st = s.used;
   DD_CK(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
   for (size_t r = 0; r < p->ranges.size(); ++r) {
@@ -828,12 +846,151 @@ int dd_plan_model(dd_plan_t p, int32_t range, int64_t nout, dd_launch_model_t* o
   for (int64_t rr = p->row0[range]; rr < p->row0[range] + R.n_trials; ++rr)
     for (int c = 0; c < p->C; ++c) smax = std::max<int64_t>(smax, p->h_shifts[rr * p->C + c]);
   const int es = R.decimation > 1 ? 2 : 1;
-  out->dram_bytes = nout > 0 ? (double)p->C * (double)(nout + smax) * es + 4.0 * out->outputs : 0;
+  // written per output: the int32 series, or, fused, a 4-byte sum and a 1-byte sample per
+  // (width, peak block) (and the series if kept)
+  double out_bytes = 4.0 * out->outputs;
+  if (k.fused) {
+    const double blocks = (double)R.n_trials * (double)((nout + p->opts.peak_block - 1) /
+                                                        p->opts.peak_block);
+    out_bytes = 5.0 * k.nw * blocks + (p->fused_series ? out_bytes : 0.0);
+    out->fused = 1;
+  }
+  out->dram_bytes = nout > 0 ? (double)p->C * (double)(nout + smax) * es + out_bytes : 0;
   if (k.tiled && nout > 0) {
     const double rows = (double)((nout + k.tt - 1) / k.tt);
     out->smem_wavefronts = rows * (double)k.lsu_wavefronts;
     out->copy_bytes = rows * (double)k.copy_bytes;
   }
+  return DD_OK;
+}
+
+int dd_fuse_search(dd_plan_t p, const int32_t* widths, int32_t nwidths, uint32_t fuse_flags,
+                   int32_t* nfused) {
+  if (!p) return fail(DD_ERR_ARG, "plan is NULL");
+  if (!widths || nwidths < 1 || nwidths > ddk::kMaxWidths)
+    return fail(DD_ERR_ARG, "nwidths must be 1..%d", ddk::kMaxWidths);
+  for (int k = 0; k < nwidths; ++k) {
+    if (widths[k] < 1 || widths[k] > p->opts.max_width)
+      return fail(DD_ERR_ARG, "width %d outside 1..max_width", widths[k]);
+    if (k > 0 && widths[k] <= widths[k - 1])
+      return fail(DD_ERR_ARG, "widths must be strictly increasing");
+  }
+  if (fuse_flags & ~DD_FUSE_KEEP_SERIES) return fail(DD_ERR_ARG, "unknown fuse flags");
+  if (p->next_seq != 0)
+    return fail(DD_ERR_STATE, "dd_fuse_search must come before the plan's first dd_run");
+  if (!p->fused_widths.empty()) return fail(DD_ERR_STATE, "the plan's search is already fused");
+  DD_CK(cudaSetDevice(p->device));
+  DD_CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
+  const bool keep = (fuse_flags & DD_FUSE_KEEP_SERIES) != 0;
+  const int nr = (int)p->ranges.size();
+  std::vector<int32_t> full;  // the delay table at the padded stride, for re-planning a range
+  std::vector<RangeKernel> nk = p->rk;
+  std::vector<bool> replanned(nr, false);
+  size_t arena = 0;
+  int count = 0;
+  int rc = DD_OK;
+  for (int r = 0; r < nr && rc == DD_OK && !(p->opts.flags & DD_FLAG_NAIVE); ++r) {
+    const int d = p->ranges[r].decimation, ntr = p->ranges[r].n_trials;
+    int wd[ddk::kMaxWidths], nw = 0;
+    for (int k = 0; k < nwidths; ++k)
+      if (widths[k] >= d && widths[k] % d == 0) wd[nw++] = widths[k] / d;
+    if (nw == 0 || wd[nw - 1] > 512 || !nk[r].tiled) continue;
+    RangeKernel& K = nk[r];
+    if (!(K.tt == 512 && K.trials == 64 && K.threads == 512)) {
+      // the fused form exists for the 64 x 512 x 512 shape: plan the range on it
+      if (full.empty()) {
+        full.resize((size_t)p->total_rows * p->Cp);
+        const cudaError_t e = cudaMemcpy(full.data(), p->d_shifts, sizeof(int32_t) * full.size(),
+                                         cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+          rc = fail(DD_ERR_CUDA, "delay table: %s", cudaGetErrorString(e));
+          break;
+        }
+      }
+      RangeKernel k2;
+      bool ok = false;
+      rc = plan_tiled_shape(&full[(size_t)p->row0[r] * p->Cp], ntr, p->Cp, d, 512, 64, 512, &k2,
+                            &ok);
+      if (rc || !ok) continue;
+      K = k2;
+      replanned[r] = true;
+    }
+    const int hp = (int)round_up(wd[nw - 1], 32);
+    int32_t e_off = 0;
+    size_t fsmem = 0;
+    if (!ddk::fused_smem(d > 1, K.row_slot, K.zcap, K.nstage, hp, &e_off, &fsmem)) {
+      if (replanned[r]) {  // keep the range as it was planned
+        cudaFree(K.d_tabs);
+        K = p->rk[r];
+        replanned[r] = false;
+      }
+      continue;
+    }
+    const cudaError_t e = ddk::prepare_fused(d > 1, K.nstage, fsmem);
+    if (e != cudaSuccess) {
+      rc = fail(DD_ERR_CUDA, "fused kernel set-up: %s", cudaGetErrorString(e));
+      break;
+    }
+    K.fused = true;
+    K.nw = nw;
+    for (int k = 0; k < nw; ++k) K.wd[k] = wd[k];
+    K.hist = wd[nw - 1];
+    K.hp = hp;
+    K.e_off = e_off;
+    K.fsmem = fsmem;
+    // record sizes for the longest window (L / d outputs)
+    const int64_t nmax = p->L / d;
+    const int ntx = (ntr + 63) / 64, ntt = (int)((nmax + 511) / 512);
+    K.smax = ddk::fused_segments(ntx, ntt, p->sms, ntt);
+    const int64_t nblk = (nmax + p->opts.peak_block - 1) / p->opts.peak_block;
+    const size_t recs = (size_t)ntr * nw * (size_t)nblk;
+    K.key_off = arena;
+    arena = (size_t)round_up((int64_t)(arena + 4 * recs), 256);
+    K.off_off = arena;
+    arena = (size_t)round_up((int64_t)(arena + recs), 256);
+    K.edge_off = arena;
+    arena = (size_t)round_up(
+        (int64_t)(arena + (size_t)K.smax * ntx * 2 * 64 * (size_t)K.hist * 4), 256);
+    ++count;
+  }
+  // series: fused ranges keep none unless asked to
+  std::vector<int64_t> off(nr, 0);
+  int64_t elems = 0;
+  for (int r = 0; r < nr; ++r) {
+    if (nk[r].fused && !keep) continue;
+    off[r] = elems;
+    elems += p->series_stride[r] * p->ranges[r].n_trials;
+  }
+  std::vector<int32_t*> series(p->slots.size(), nullptr);
+  std::vector<uint8_t*> fused(p->slots.size(), nullptr);
+  for (size_t i = 0; i < p->slots.size() && rc == DD_OK && count > 0; ++i) {
+    rc = dalloc(&series[i], sizeof(int32_t) * (size_t)elems, "series");
+    if (rc == DD_OK) rc = dalloc(&fused[i], arena, "fused search records");
+  }
+  if (rc != DD_OK) {
+    for (size_t i = 0; i < series.size(); ++i) {
+      cudaFree(series[i]);
+      cudaFree(fused[i]);
+    }
+    for (int r = 0; r < nr; ++r)
+      if (replanned[r]) cudaFree(nk[r].d_tabs);
+    return rc;
+  }
+  p->fused_widths.assign(widths, widths + nwidths);
+  p->fused_series = keep;
+  if (count > 0) {
+    for (int r = 0; r < nr; ++r)
+      if (replanned[r]) cudaFree(p->rk[r].d_tabs);
+    p->rk = nk;
+    p->series_off = off;
+    p->series_elems = elems;
+    for (size_t i = 0; i < p->slots.size(); ++i) {
+      cudaFree(p->slots[i].series);
+      p->slots[i].series = series[i];
+      p->slots[i].fused = fused[i];
+    }
+  }
+  if (nfused) *nfused = count;
   return DD_OK;
 }
 
@@ -941,7 +1098,30 @@ static int run_impl(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda
       A.nstage = K.nstage;
       A.tabs = K.d_tabs;
       A.err = p->err_word ? p->err_word : reinterpret_cast<int32_t*>(s.d_count + 1);
-      if (defer && K.tt == 512 && K.trials == 64 && K.threads == 512) {
+      if (K.fused) {
+        ddk::FusedArgs F;
+        std::memset(&F, 0, sizeof F);
+        F.key = reinterpret_cast<uint32_t*>(s.fused + K.key_off);
+        F.off = s.fused + K.off_off;
+        F.edge = reinterpret_cast<uint32_t*>(s.fused + K.edge_off);
+        F.block = p->opts.peak_block;
+        F.nblk = (R.nout + F.block - 1) / F.block;
+        F.nw = K.nw;
+        for (int k = 0; k < K.nw; ++k) F.wd[k] = K.wd[k];
+        F.hist = K.hist;
+        F.hp = K.hp;
+        const int ntx = (R.n_trials + 63) / 64, ntt = (int)((R.nout + 511) / 512);
+        F.nsegs = ddk::fused_segments(ntx, ntt, p->sms, K.smax);
+        F.seg_tiles = (ntt + F.nsegs - 1) / F.nsegs;
+        F.keep_series = p->fused_series ? 1 : 0;
+        F.e_off = K.e_off;
+        if (!p->fused_series) {
+          A.y = nullptr;
+          A.y_stride = 0;
+        }
+        DD_CK(ddk::launch_fused(A, F, R.is_u16, K.fsmem, st));
+        p->launches += F.nsegs > 1 ? 2 : 1;
+      } else if (defer && K.tt == 512 && K.trials == 64 && K.threads == 512) {
         ddk::DeferredTile dt;
         dt.args = A;
         dt.is_u16 = R.is_u16;
@@ -986,6 +1166,8 @@ int dd_series(dd_plan_t p, int32_t range, const int32_t** dev_ptr, int64_t* len,
   if (!p) return fail(DD_ERR_ARG, "plan is NULL");
   if (range < 0 || range >= (int32_t)p->ranges.size()) return fail(DD_ERR_ARG, "bad range");
   if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
+  if (p->rk[range].fused && !p->fused_series)
+    return fail(DD_ERR_STATE, "range %d's search is fused: its series are not kept", (int)range);
   const Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
   const int d = p->ranges[range].decimation;
   if (dev_ptr) *dev_ptr = s.series + p->series_off[range];
@@ -1027,6 +1209,15 @@ int sps_run_ex(dd_plan_t p, const int32_t* widths, int32_t nwidths, float thresh
   if (p->next_seq == 0) return fail(DD_ERR_STATE, "no chunk has been run");
   Slot& s = p->slots[(p->next_seq - 1) % p->slots.size()];
   if (s.searched) return fail(DD_ERR_STATE, "the latest chunk was already searched");
+  bool any_fused = false;
+  for (const auto& k : p->rk) any_fused |= k.fused;
+  if (any_fused) {
+    if (p->fused_widths != std::vector<int32_t>(widths, widths + nwidths))
+      return fail(DD_ERR_ARG, "the plan's search is fused with other widths (dd_fuse_search)");
+    if (clipped && !p->fused_series)
+      return fail(DD_ERR_STATE, "clipped statistics need the series, which a fused plan does not "
+                                "keep (DD_FUSE_KEEP_SERIES)");
+  }
   DD_CK(cudaSetDevice(p->device));
   cudaStream_t st = s.used;
   DD_CK(cudaMemsetAsync(s.d_count, 0, sizeof(unsigned long long), st));
@@ -1039,6 +1230,30 @@ int sps_run_ex(dd_plan_t p, const int32_t* widths, int32_t nwidths, float thresh
       if (widths[k] >= d && widths[k] % d == 0) a.wd[a.nw++] = widths[k] / d;
     a.n = (s.hi - s.lo) / d;
     if (a.nw == 0 || a.n <= 0) continue;
+    const RangeKernel& K = p->rk[r];
+    if (K.fused && !clipped) {
+      ddk::SpsFusedArgs f;
+      std::memset(&f, 0, sizeof f);
+      f.key = reinterpret_cast<const uint32_t*>(s.fused + K.key_off);
+      f.off = s.fused + K.off_off;
+      f.block = p->opts.peak_block;
+      f.n = a.n;
+      f.nblk = (a.n + f.block - 1) / f.block;
+      f.mom = s.mom + p->row0[r];
+      f.n_trials = p->ranges[r].n_trials;
+      f.range = (int32_t)r;
+      f.d = d;
+      f.J0 = s.lo / d;
+      f.nw = a.nw;
+      for (int k = 0; k < a.nw; ++k) f.wd[k] = a.wd[k];
+      f.threshold = threshold;
+      f.cands = s.cands;
+      f.count = s.d_count;
+      f.cap = p->opts.max_cands;
+      DD_CK(ddk::launch_sps_fused(f, st));
+      p->launches += 1;
+      continue;
+    }
     a.y = s.series + p->series_off[r];
     a.stride = p->series_stride[r];
     a.mom = s.mom + p->row0[r];

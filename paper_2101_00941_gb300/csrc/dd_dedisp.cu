@@ -442,9 +442,160 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
   }
 }
 
-template <typename T, int TT, int NS, int D, int NT>
+// ---- search fused into the tile (Sec. 2.2 boxcars over the series the tile has just summed)
+//
+// Per trial the warp forms the tile's inclusive prefix sums P[j] (uint32, relative to the tile's
+// start: exact differences since every boxcar sum is < 2^31) in a shared-memory row, preceded by
+// the `hist` prefix sums of the previous tile in this tile's frame (P[m] = -(sum of the previous
+// tile's outputs after m), m = -hist .. -1). Then B_w[j] = P[j] - P[j - w] for every width, and
+// per peak block the largest B_w + 1 (0: no valid sample) and its earliest sample are stored.
+// Valid samples: inside the window, j >= w - 1 in the window (the boxcars of Sec. 2.2 reading),
+// and, in the first tile of a segment (no previous tile), boxcars inside the tile only; the
+// others are k_fused_edges' work.
+
+// Largest key over aligned groups of B lanes (B a power of two <= 32) and, for the group's
+// first lane, the group's earliest lane holding it.
+__device__ __forceinline__ uint32_t group_max(uint32_t key, int B, int lane, int* first) {
+  uint32_t mx = key;
+  if (B == 32) {
+    mx = __reduce_max_sync(0xffffffffu, key);
+  } else {
+    for (int o = B >> 1; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const uint32_t bal = __ballot_sync(0xffffffffu, key == mx);
+  const uint32_t gm = B == 32 ? 0xffffffffu : ((1u << B) - 1u);
+  *first = __ffs((bal >> (lane & ~(B - 1))) & gm) - 1;
+  return mx;
+}
+
+// Head and tail buffers of CTA (trial tile bx, segment seg): [64][hist] each.
+__device__ __forceinline__ uint32_t* fused_edge(const FusedArgs& f, int ntx, int bx, int seg) {
+  return f.edge + ((size_t)seg * ntx + bx) * 2 * kMaxTileTrials * (size_t)f.hist;
+}
+
+template <int TT, int W, int kTPW, int KT>
+__device__ __forceinline__ void fused_search(const TiledArgs& a, const FusedArgs& f,
+                                             const uint32_t (&acc)[kTPW][KT],
+                                             unsigned char* smem, int bx, int by, bool first,
+                                             int trial0, int ntr, int64_t j0, int warp,
+                                             int lane) {
+  constexpr int KP = KT / 2;
+  const int hist = f.hist, HP = f.hp, Bk = f.block, nw = f.nw;
+  const int wmax = f.wd[nw - 1];
+  const int ntx = (a.n_trials + kMaxTileTrials - 1) / kMaxTileTrials;
+  const int seg = by / f.seg_tiles;
+  uint32_t* head = fused_edge(f, ntx, bx, seg);
+  uint32_t* tail = head + kMaxTileTrials * (size_t)hist;
+  uint32_t* E = reinterpret_cast<uint32_t*>(smem + f.e_off) + (size_t)warp * (HP + TT) + HP;
+  const int64_t nout = a.nout;
+#pragma unroll
+  for (int q = 0; q < kTPW; ++q) {  // unrolled: acc stays in registers
+    const int t = warp + W * q;
+    if (t >= ntr) break;  // uniform in the warp; later q only larger
+    // inclusive prefix sums of the tile; lane l holds outputs 2(l + 32k) and 2(l + 32k) + 1
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const uint32_t ev = acc[q][2 * k], od = acc[q][2 * k + 1];
+      uint32_t incl = ev + od;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+      }
+      const uint32_t po = carry + incl;
+      *reinterpret_cast<uint2*>(E + 2 * (lane + 32 * k)) = make_uint2(po - od, po);
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    // the previous tile's prefix sums in this tile's frame (none before a segment's first tile:
+    // no valid boxcar reads them there)
+    uint32_t* tl = tail + (size_t)t * hist;
+    for (int i = lane; i < hist; i += 32) E[i - hist] = first ? 0u : tl[i];
+    __syncwarp();
+    if (first && seg > 0) {
+      uint32_t* hd = head + (size_t)t * hist;
+      for (int i = lane; i < hist; i += 32) hd[i] = E[i];
+    }
+    // this tile's last prefix sums in the next tile's frame (P[TT + m] - P[TT - 1])
+    for (int i = lane; i < hist; i += 32) tl[i] = E[TT - hist + i] - carry;
+    const int64_t rowk = (int64_t)(trial0 + t) * nw;
+#pragma unroll 1
+    for (int m = 0; m < TT / 32; ++m) {
+      const int64_t jb = j0 + 32 * m;  // the pass's first window sample
+      if (jb >= nout) break;           // uniform
+      const int jl = 32 * m + lane;
+      const int64_t jg = jb + lane;
+      const bool interior = jb + 32 <= nout && jb >= wmax - 1 && (!first || 32 * m >= wmax - 1);
+      const uint32_t p1 = E[jl] + 1u;
+      const bool leader = (lane & (Bk - 1)) == 0 && jg < nout;
+      const int64_t blk = jg / Bk;
+#pragma unroll 1
+      for (int k = 0; k < nw; ++k) {
+        const int w = f.wd[k];
+        uint32_t key = p1 - E[jl - w];
+        if (!interior) {
+          const bool valid = jg < nout && jg >= w - 1 && (!first || jl >= w - 1);
+          key = valid ? key : 0u;
+        }
+        int fo;
+        const uint32_t mx = group_max(key, Bk, lane, &fo);
+        if (leader) {
+          const int64_t idx = (rowk + k) * f.nblk + blk;
+          f.key[idx] = mx;
+          f.off[idx] = (uint8_t)fo;
+        }
+      }
+    }
+    __syncwarp();  // the row is rewritten for the warp's next trial
+  }
+  // the rows overlay the staging buffers that the next tile's tensor copies fill
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Boxcars of a segment's first tile that start in the previous segment: per (boundary, trial),
+// width w, samples j < w - 1 of the tile, B = head[j] - tail[hist + j - w], merged into the
+// block's record (these samples precede every sample the fused pass saw in the block, so they
+// win ties). One CTA per (trial tile, boundary), one warp per trial.
+__global__ void __launch_bounds__(512) k_fused_edges(const __grid_constant__ TiledArgs a,
+                                                     const __grid_constant__ FusedArgs f) {
+  const int bx = blockIdx.x, seg = blockIdx.y + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t J = (int64_t)seg * f.seg_tiles * 512;
+  if (J >= a.nout) return;
+  const int ntx = gridDim.x;
+  const int hist = f.hist, Bk = f.block;
+  const uint32_t* head = fused_edge(f, ntx, bx, seg);
+  const uint32_t* tail = fused_edge(f, ntx, bx, seg - 1) + kMaxTileTrials * (size_t)hist;
+  for (int t = warp; t < kMaxTileTrials; t += 16) {
+    const int trial = bx * kMaxTileTrials + t;
+    if (trial >= a.n_trials) break;
+    const uint32_t* hd = head + (size_t)t * hist;
+    const uint32_t* tl = tail + (size_t)t * hist;
+    for (int k = 0; k < f.nw; ++k) {
+      const int w = f.wd[k];
+      for (int jb = 0; jb < w - 1; jb += 32) {
+        const int jl = jb + lane;
+        const int64_t jg = J + jl;
+        const bool valid = jl < w - 1 && jg < a.nout;
+        const uint32_t key = valid ? hd[jl] + 1u - tl[hist + jl - w] : 0u;
+        int fo;
+        const uint32_t mx = group_max(key, Bk, lane, &fo);
+        if ((lane & (Bk - 1)) == 0 && jg < a.nout && mx != 0) {
+          const int64_t idx = ((int64_t)trial * f.nw + k) * f.nblk + jg / Bk;
+          if (mx >= f.key[idx]) {
+            f.key[idx] = mx;
+            f.off[idx] = (uint8_t)fo;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int TT, int NS, int D, int NT, bool FUSED = false>
 __device__ __forceinline__ bool tile_body(const TiledArgs& a, int bx, int by,
-                                          unsigned char* smem, bool reuse) {
+                                          unsigned char* smem, bool reuse,
+                                          const FusedArgs* f = nullptr, bool first = false) {
   constexpr int KT = TT / 32;       // outputs per lane and trial
   constexpr int KP = TT / 64;       // pair words per lane and trial
   constexpr int W = NT / 32;        // warps
@@ -588,13 +739,16 @@ __device__ __forceinline__ bool tile_body(const TiledArgs& a, int bx, int by,
       int32_t* yr = a.y + (int64_t)(trial0 + t) * a.y_stride;
       unsigned long long s1 = 0, lo = 0, hi = 0;
 #pragma unroll
+      const bool store = !FUSED || f->keep_series;
       for (int k = 0; k < KP; ++k) {
         const int64_t j = j0 + 2 * (lane + 32 * k);
-        if (j + 1 < a.nout)
+        if (!store) {
+        } else if (j + 1 < a.nout) {
           *reinterpret_cast<int2*>(yr + j) = make_int2((int32_t)acc[q][2 * k],
                                                        (int32_t)acc[q][2 * k + 1]);
-        else if (j < a.nout)
+        } else if (j < a.nout) {
           yr[j] = (int32_t)acc[q][2 * k];
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (j + h < a.nout) {
@@ -623,6 +777,8 @@ __device__ __forceinline__ bool tile_body(const TiledArgs& a, int bx, int by,
       }
     }
   }
+  if constexpr (FUSED)
+    fused_search<TT, W, kTPW, KT>(a, *f, acc, smem, bx, by, first, trial0, ntr, j0, warp, lane);
   return true;
 }
 
@@ -667,6 +823,19 @@ __global__ void __launch_bounds__(NT, 1) k_dedisp_persistent(const __grid_consta
       break;  // a bounded wait ran out (uniform): the error bit is set
     reuse = true;
   }
+}
+
+// Fused form: CTA (x, y) runs trial tile x over time tiles y * seg_tiles .. (y + 1) * seg_tiles
+// - 1 in order, each tile's search reading the previous tile's prefix sums (FusedArgs).
+template <typename T, int NS>
+__global__ void __launch_bounds__(512, 1)
+    k_dedisp_fused(const __grid_constant__ TiledArgs a, const __grid_constant__ FusedArgs f) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int ntt = (int)((a.nout + 511) / 512);
+  const int y0 = blockIdx.y * f.seg_tiles, y1 = min(ntt, y0 + f.seg_tiles);
+  for (int y = y0; y < y1; ++y)
+    if (!tile_body<T, 512, NS, 64, 512, true>(a, blockIdx.x, y, smem, y > y0, &f, y == y0))
+      break;  // a bounded wait ran out (uniform): the error bit is set
 }
 
 template <typename T, int TT, int NS, int D, int NT>
@@ -1084,6 +1253,83 @@ cudaError_t make_ring_map(CUtensorMap* map, const void* ring, int is_u16, int64_
          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+bool fused_smem(int is_u16, int row_slot, int zcap, int nstage, int hp, int32_t* e_off,
+                size_t* smem) {
+  const SmemLayout L = smem_layout(is_u16 ? 2 : 1, 4, row_slot, zcap, nstage);
+  const size_t rows = (size_t)kWarps * (hp + 512) * sizeof(uint32_t);
+  size_t total = L.total, off = L.raw;
+  if (L.tab - L.raw < rows) {  // the staging area is too small: the rows go after it
+    off = L.total;
+    total = L.total + rows;
+  }
+  if (total > kSmemLimit) return false;
+  *e_off = (int32_t)off;
+  *smem = total;
+  return true;
+}
+
+namespace {
+
+template <typename T, int NS>
+cudaError_t prepare_fused_t() {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dedisp_fused<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t prepare_fused(int is_u16, int nstage, size_t smem) {
+  if (smem > kSmemLimit) return cudaErrorInvalidValue;
+  if (!is_u16 && nstage == 4) return prepare_fused_t<uint8_t, 4>();
+  if (!is_u16 && nstage == 3) return prepare_fused_t<uint8_t, 3>();
+  if (is_u16 && nstage == 4) return prepare_fused_t<uint16_t, 4>();
+  if (is_u16 && nstage == 3) return prepare_fused_t<uint16_t, 3>();
+  return cudaErrorInvalidValue;
+}
+
+int fused_segments(int ntx, int ntt, int sms, int smax) {
+  int best = 1;
+  int64_t best_cost = -1;
+  for (int s = 1; s <= std::min(ntt, std::max(1, smax)); ++s) {
+    const int seg = (ntt + s - 1) / s;
+    const int used = (ntt + seg - 1) / seg;  // segments that get tiles
+    const int64_t waves = ((int64_t)ntx * used + sms - 1) / sms;
+    const int64_t cost = waves * seg;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = used;
+    }
+  }
+  return best;
+}
+
+cudaError_t launch_fused(const TiledArgs& a, const FusedArgs& f, int is_u16, size_t smem,
+                         cudaStream_t st) {
+  if (a.nout <= 0 || a.n_trials <= 0) return cudaSuccess;
+  const int ntx = (a.n_trials + kMaxTileTrials - 1) / kMaxTileTrials;
+  const int ntt = (int)((a.nout + 511) / 512);
+  if (f.nsegs < 1 || (int64_t)f.nsegs * f.seg_tiles < ntt ||
+      (int64_t)(f.nsegs - 1) * f.seg_tiles >= ntt || f.hist < 1 || f.hist > 512 ||
+      f.hp < f.hist || f.nw < 1 || f.wd[f.nw - 1] != f.hist)
+    return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)ntx, (unsigned)f.nsegs);
+  if (!is_u16 && a.nstage == 4) k_dedisp_fused<uint8_t, 4><<<grid, 512, smem, st>>>(a, f);
+  else if (!is_u16 && a.nstage == 3) k_dedisp_fused<uint8_t, 3><<<grid, 512, smem, st>>>(a, f);
+  else if (is_u16 && a.nstage == 4) k_dedisp_fused<uint16_t, 4><<<grid, 512, smem, st>>>(a, f);
+  else if (is_u16 && a.nstage == 3) k_dedisp_fused<uint16_t, 3><<<grid, 512, smem, st>>>(a, f);
+  else return cudaErrorInvalidValue;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || f.nsegs < 2) return e;
+  k_fused_edges<<<dim3((unsigned)ntx, (unsigned)(f.nsegs - 1)), 512, 0, st>>>(a, f);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tiled(const TiledArgs& a, int is_u16, int tt, int D, int nt,

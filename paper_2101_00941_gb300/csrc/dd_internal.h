@@ -103,6 +103,49 @@ struct TiledArgs {
   CUtensorMap rows;        // the ring as [Cp][xd_stride / seg][seg] (make_ring_map)
 };
 
+// Search fused into the tiled kernel (64 x 512 tiles, 16 warps): one CTA walks a segment of
+// consecutive time tiles of one trial tile and, after each tile, records per (trial, width,
+// peak block) the block's largest boxcar sum and its earliest sample. Boxcars that reach back
+// into the previous tile read that tile's prefix sums from the CTA's tail buffer; the first tile
+// of a segment has none, and its boxcars that start before the segment are completed by
+// k_fused_edges from the previous segment's tail and this segment's head.
+struct FusedArgs {
+  uint32_t* key;           // [n_trials][nw][nblk]: 1 + the largest boxcar sum, 0 = no sample
+  uint8_t* off;            // [n_trials][nw][nblk]: its earliest sample within the block
+  uint32_t* edge;          // [nsegs][trial tiles][2][64][hist]: head, tail prefix sums per CTA
+  int64_t nblk;            // peak blocks of the window, ceil(nout / block)
+  int32_t nw;              // widths (decimated), increasing, the last <= 512
+  int32_t hist;            // the largest width: prefix sums kept from the previous tile
+  int32_t hp;              // hist rounded up to 32
+  int32_t block;           // samples per peak block (power of two <= 32)
+  int32_t seg_tiles;       // time tiles per segment
+  int32_t nsegs;           // segments (gridDim.y)
+  int32_t keep_series;     // also write the series
+  int32_t e_off;           // shared-memory byte offset of the per-warp prefix-sum rows
+  int32_t wd[kMaxWidths];
+};
+
+// The search's last step for a fused range: per (trial, peak block) the FP64 SNR of each
+// width's recorded maximum, the best over widths, and the candidate (as k_sps).
+struct SpsFusedArgs {
+  const uint32_t* key;     // FusedArgs::key
+  const uint8_t* off;
+  int64_t nblk;
+  int64_t n;               // window length
+  const Moments* mom;      // [n_trials]
+  int32_t n_trials;
+  int32_t range;
+  int32_t d;
+  int32_t block;
+  int64_t J0;
+  int32_t nw;
+  int32_t wd[kMaxWidths];
+  float threshold;
+  dd_cand_t* cands;
+  unsigned long long* count;
+  int64_t cap;
+};
+
 // Arguments of the persistent tiled kernel: a device work list over many ranges (of many plans)
 // of one instance (data type, tile shape, staging buffers). Segment k covers every tile of
 // descs[seg_desc[k]]: items seg_first[k] .. seg_first[k + 1] - 1 (trial tiles fastest).
@@ -154,6 +197,19 @@ cudaError_t launch_tiled_persistent(const PersistArgs& p, int is_u16, int tt, in
                                     int trials, int threads, size_t smem, int ctas,
                                     cudaStream_t st);
 size_t tiled_smem_bytes(int is_u16, int row_slot, int zcap, int nstage);
+// Fused search (64 x 512 x 512 instances): where the per-warp prefix-sum rows go in shared
+// memory (inside the staging area when it is large enough, else after it) and the launch's
+// dynamic shared memory; false if that exceeds what a CTA may plan for.
+bool fused_smem(int is_u16, int row_slot, int zcap, int nstage, int hp, int32_t* e_off,
+                size_t* smem);
+cudaError_t prepare_fused(int is_u16, int nstage, size_t smem);
+// Time segments of a fused launch: minimises (waves of one CTA per SM) x (tiles per segment)
+// for ntx trial tiles and ntt time tiles, at most smax segments.
+int fused_segments(int ntx, int ntt, int sms, int smax);
+// The fused dedispersion launch, grid (trial tiles, f.nsegs), then the segment-edge pass.
+cudaError_t launch_fused(const TiledArgs& a, const FusedArgs& f, int is_u16, size_t smem,
+                         cudaStream_t st);
+cudaError_t launch_sps_fused(const SpsFusedArgs& a, cudaStream_t st);
 
 // Tensor map of a channel-major ring (uint8, or uint16 when is_u16) for the tiled kernel's
 // stage copies: dims {128-byte segment, segments per row, cpad rows}, box {segment, nseg, 16}.

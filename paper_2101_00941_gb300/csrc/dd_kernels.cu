@@ -410,6 +410,20 @@ __device__ __forceinline__ double u128_to_f64(unsigned long long hi, unsigned lo
   return ldexp(__ull2double_rn(top | sticky), sh);
 }
 
+// sqrt(n*S2 - S1^2) of a window's moments, V = n*S2 - S1^2 formed exactly in 128 bits (S1 >= 0
+// because every series value is a sum of non-negative samples) and rounded once to FP64; 0 for a
+// constant series.
+__device__ __forceinline__ double window_sqrt_var(const Moments& m, long long n) {
+  const unsigned long long un = (unsigned long long)n, us1 = m.s1;
+  const unsigned long long p_lo = un * m.s2lo;
+  const unsigned long long p_hi = __umul64hi(un, m.s2lo) + un * m.s2hi;
+  const unsigned long long q_lo = us1 * us1, q_hi = __umul64hi(us1, us1);
+  const unsigned long long v_lo = p_lo - q_lo;
+  const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
+  if (v_lo == 0 && v_hi == 0) return 0.0;
+  return sqrt(u128_to_f64(v_hi, v_lo));
+}
+
 constexpr int kSpsThreads = 256;
 constexpr int kSpsSeg = kSpsThreads * 16;         // window samples per pass (16 per thread)
 constexpr int kSpsPad = 3;                        // aligns P[1 + hist + 4k] to 16 bytes
@@ -523,16 +537,8 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
   if (a.wst == nullptr) {
     const Moments m = a.mom[i];
     const long long s1 = (long long)m.s1;
-    // V = n*S2 - S1^2 in 128 bits (exact; S1 >= 0 because every series value is a sum of
-    // non-negative samples)
-    const unsigned long long un = (unsigned long long)n, us1 = (unsigned long long)s1;
-    const unsigned long long p_lo = un * m.s2lo;
-    const unsigned long long p_hi = __umul64hi(un, m.s2lo) + un * m.s2hi;
-    const unsigned long long q_lo = us1 * us1, q_hi = __umul64hi(us1, us1);
-    const unsigned long long v_lo = p_lo - q_lo;
-    const unsigned long long v_hi = p_hi - q_hi - (p_lo < q_lo ? 1ull : 0ull);
-    if (v_lo == 0 && v_hi == 0) return;  // constant series: no candidates
-    const double sq = sqrt(u128_to_f64(v_hi, v_lo));
+    const double sq = window_sqrt_var(m, n);
+    if (sq == 0.0) return;  // constant series: no candidates
     if (tid < a.nw) {
       const int w = a.wd[tid];
       den[tid] = sqrt((double)w) * sq;
@@ -655,6 +661,65 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
     __syncthreads();  // every read of this pass's P is done
     // the last H + 1 entries become the next pass's history (P[kSpsSeg] = sum before it)
     for (int k = tid; k <= H; k += kSpsThreads) P[k] = P[kSpsSeg + k];
+  }
+}
+
+// The search's last step on a range whose block maxima the fused dedispersion kernel recorded:
+// one CTA per trial, one thread per peak block. The block's candidate is, over the widths, the
+// recorded largest boxcar sum's SNR (the SNR grows with the sum at a fixed width, and the
+// recorded sample is the earliest holding it), with k_sps's statistics, evaluation order and
+// tie rules, so the candidates are the ones k_sps finds on the same series.
+__global__ void __launch_bounds__(kSpsThreads) k_sps_fused(const SpsFusedArgs a) {
+  __shared__ double den[kMaxWidths];
+  __shared__ long long ca[kMaxWidths], cb[kMaxWidths];
+  const int32_t i = blockIdx.x;
+  const int tid = threadIdx.x;
+  const long long n = a.n;
+  if (n <= 0) return;
+  const Moments m = a.mom[i];
+  const double sq = window_sqrt_var(m, n);
+  if (sq == 0.0) return;  // constant series: no candidates
+  if (tid < a.nw) {
+    const int w = a.wd[tid];
+    den[tid] = sqrt((double)w) * sq;
+    ca[tid] = n;
+    cb[tid] = (long long)w * (long long)m.s1;
+  }
+  __syncthreads();
+  const double thr = (double)a.threshold;
+  const int64_t row = (int64_t)i * a.nw;
+  for (int64_t b = tid; b < a.nblk; b += kSpsThreads) {
+    double bs = 0.0;
+    long long bj = 0;
+    int bwid = 0;
+    bool have = false;
+    for (int k = 0; k < a.nw; ++k) {
+      const uint32_t key = a.key[(row + k) * a.nblk + b];
+      if (key == 0) continue;
+      const long long best = (long long)(key - 1u);
+      const long long jk = b * a.block + a.off[(row + k) * a.nblk + b];
+      const long long num = ca[k] * best - cb[k];
+      const double snr = (double)num / den[k];
+      if (!have || snr > bs || (snr == bs && jk < bj)) {
+        have = true;
+        bs = snr;
+        bj = jk;
+        bwid = a.wd[k];
+      }
+    }
+    if (have && bs >= thr) {
+      const unsigned long long idx = atomicAdd(a.count, 1ull);
+      if ((long long)idx < a.cap) {
+        dd_cand_t cd;
+        cd.trial = i;
+        cd.range = a.range;
+        cd.t_start = (a.J0 + bj - bwid + 1) * (long long)a.d;
+        cd.width = bwid * a.d;
+        cd.pad = 0;
+        cd.snr = bs;
+        a.cands[idx] = cd;
+      }
+    }
   }
 }
 
@@ -806,6 +871,14 @@ cudaError_t launch_sps(const SpsArgs& a, cudaStream_t st) {
     return cudaErrorInvalidValue;
   const size_t smem = sizeof(uint32_t) * (size_t)(kSpsPad + 1 + a.hist + kSpsSeg);
   k_sps<<<a.n_trials, kSpsThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sps_fused(const SpsFusedArgs& a, cudaStream_t st) {
+  if (a.n <= 0 || a.n_trials <= 0 || a.nw <= 0) return cudaSuccess;
+  if (a.block < 1 || a.block > 32 || a.nblk != (a.n + a.block - 1) / a.block)
+    return cudaErrorInvalidValue;
+  k_sps_fused<<<a.n_trials, kSpsThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
