@@ -453,6 +453,22 @@ __device__ __forceinline__ void build_stage(const StageTab& tb, const AddrTab& a
 // and, in the first tile of a segment (no previous tile), boxcars inside the tile only; the
 // others are k_fused_edges' work.
 
+// L2 evict-last access policy for the tail buffers: rewritten every tile and read back one tile
+// later, while the streamed channel rows pass through L2 in between.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_keep(uint32_t* p, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
 // Largest key over aligned groups of B lanes (B a power of two <= 32) and, for the group's
 // first lane, the group's earliest lane holding it.
 __device__ __forceinline__ uint32_t group_max(uint32_t key, int B, int lane, int* first) {
@@ -488,10 +504,18 @@ __device__ __forceinline__ void fused_search(const TiledArgs& a, const FusedArgs
   uint32_t* tail = head + kMaxTileTrials * (size_t)hist;
   uint32_t* E = reinterpret_cast<uint32_t*>(smem + f.e_off) + (size_t)warp * (HP + TT) + HP;
   const int64_t nout = a.nout;
+  const uint64_t pol = l2_keep_policy();
 #pragma unroll
   for (int q = 0; q < kTPW; ++q) {  // unrolled: acc stays in registers
     const int t = warp + W * q;
     if (t >= ntr) break;  // uniform in the warp; later q only larger
+    uint32_t* tl = tail + (size_t)t * hist;
+    uint32_t hv[16];  // hist <= 512; independent loads, all in flight before the scan
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = lane + 32 * r;
+      hv[r] = (!first && i < hist) ? ld_keep(tl + i, pol) : 0u;
+    }
     // inclusive prefix sums of the tile; lane l holds outputs 2(l + 32k) and 2(l + 32k) + 1
     uint32_t carry = 0;
 #pragma unroll
@@ -509,15 +533,18 @@ __device__ __forceinline__ void fused_search(const TiledArgs& a, const FusedArgs
     }
     // the previous tile's prefix sums in this tile's frame (none before a segment's first tile:
     // no valid boxcar reads them there)
-    uint32_t* tl = tail + (size_t)t * hist;
-    for (int i = lane; i < hist; i += 32) E[i - hist] = first ? 0u : tl[i];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = lane + 32 * r;
+      if (i < hist) E[i - hist] = hv[r];
+    }
     __syncwarp();
     if (first && seg > 0) {
       uint32_t* hd = head + (size_t)t * hist;
       for (int i = lane; i < hist; i += 32) hd[i] = E[i];
     }
     // this tile's last prefix sums in the next tile's frame (P[TT + m] - P[TT - 1])
-    for (int i = lane; i < hist; i += 32) tl[i] = E[TT - hist + i] - carry;
+    for (int i = lane; i < hist; i += 32) st_keep(tl + i, E[TT - hist + i] - carry, pol);
     const int64_t rowk = (int64_t)(trial0 + t) * nw;
 #pragma unroll 1
     for (int m = 0; m < TT / 32; ++m) {
