@@ -1008,9 +1008,10 @@ static int run_impl(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda
   const int64_t seq = p->next_seq;
   Slot& s = p->slots[seq % p->slots.size()];
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : s.stream;
-  // the slot's previous chunk (possibly on another stream) must be finished with its buffers
+  // the slot's previous chunk (possibly on another stream) must be finished with its buffers;
+  // the wait for the previous chunk's history comes after the copy of this chunk's samples, so
+  // that the copy does not queue behind the history chain
   if (s.seq >= 0) DD_CK(cudaStreamWaitEvent(st, s.ev_free, 0));
-  if (seq > 0) DD_CK(cudaStreamWaitEvent(st, p->ev_hist, 0));
 
   cudaPointerAttributes attr;
   DD_CK(cudaPointerGetAttributes(&attr, chunk));
@@ -1034,6 +1035,7 @@ static int run_impl(dd_plan_t p, const uint8_t* chunk, int64_t nsamp, void* cuda
   // the slot's kernel error bits describe this chunk only
   if (!p->err_word) DD_CK(cudaMemsetAsync(s.d_count + 1, 0, sizeof(unsigned long long), st));
   const int64_t H = p->H;
+  if (seq > 0) DD_CK(cudaStreamWaitEvent(st, p->ev_hist, 0));
   if (seq > 0 && H > 0)
     DD_CK(cudaMemcpy2DAsync(s.ring1, p->R1, p->hist, H, H, p->Cp, cudaMemcpyDeviceToDevice, st));
   DD_CK(ddk::launch_corner_turn(src, nsamp, p->C, s.ring1, p->R1, H, st));
