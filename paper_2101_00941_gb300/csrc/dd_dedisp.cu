@@ -546,30 +546,66 @@ __device__ __forceinline__ void fused_search(const TiledArgs& a, const FusedArgs
     // this tile's last prefix sums in the next tile's frame (P[TT + m] - P[TT - 1])
     for (int i = lane; i < hist; i += 32) st_keep(tl + i, E[TT - hist + i] - carry, pol);
     const int64_t rowk = (int64_t)(trial0 + t) * nw;
+    // one lane per item: a 32-sample block is two items of 16 samples (lanes b and b + 16), a
+    // smaller block one item; each lane visits its samples from (lane mod P) on, so the 32 lanes
+    // of a load read 32 different banks, and keeps per width the largest key and, on ties, the
+    // earliest sample
+    const int P = Bk == 32 ? 16 : Bk;
+    const int nitems = (TT / Bk) * (Bk == 32 ? 2 : 1);
+    const bool interior = j0 >= wmax - 1 && !first && j0 + TT <= nout;
 #pragma unroll 1
-    for (int m = 0; m < TT / 32; ++m) {
-      const int64_t jb = j0 + 32 * m;  // the pass's first window sample
-      if (jb >= nout) break;           // uniform
-      const int jl = 32 * m + lane;
-      const int64_t jg = jb + lane;
-      const bool interior = jb + 32 <= nout && jb >= wmax - 1 && (!first || 32 * m >= wmax - 1);
-      const uint32_t p1 = E[jl] + 1u;
-      const bool leader = (lane & (Bk - 1)) == 0 && jg < nout;
-      const int64_t blk = jg / Bk;
+    for (int it = lane; it < nitems; it += 32) {
+      const int b = Bk == 32 ? (it & 15) : it;
+      const int h = Bk == 32 ? (it >> 4) : 0;
+      const int o0 = h * P;  // the item's first sample within its block
+      const int jl0 = b * Bk + o0;
+      uint32_t best[kMaxWidths];
+      int boff[kMaxWidths];
+#pragma unroll
+      for (int k = 0; k < kMaxWidths; ++k) best[k] = 0u, boff[k] = 32;
 #pragma unroll 1
-      for (int k = 0; k < nw; ++k) {
-        const int w = f.wd[k];
-        uint32_t key = p1 - E[jl - w];
-        if (!interior) {
-          const bool valid = jg < nout && jg >= w - 1 && (!first || jl >= w - 1);
-          key = valid ? key : 0u;
+      for (int i = 0; i < P; ++i) {
+        const int pi = (i + lane) & (P - 1);
+        const int jl = jl0 + pi, o = o0 + pi;
+        const int64_t jg = j0 + jl;
+        const uint32_t p1 = E[jl] + 1u;
+#pragma unroll
+        for (int k = 0; k < kMaxWidths; ++k) {
+          if (k < nw) {
+            const int w = f.wd[k];
+            uint32_t key = p1 - E[jl - w];
+            if (!interior) {
+              const bool valid = jg < nout && jg >= w - 1 && (!first || jl >= w - 1);
+              key = valid ? key : 0u;
+            }
+            const bool take = key > best[k] || (key == best[k] && o < boff[k]);
+            best[k] = take ? key : best[k];
+            boff[k] = take ? o : boff[k];
+          }
         }
-        int fo;
-        const uint32_t mx = group_max(key, Bk, lane, &fo);
-        if (leader) {
-          const int64_t idx = (rowk + k) * f.nblk + blk;
-          f.key[idx] = mx;
-          f.off[idx] = (uint8_t)fo;
+      }
+      if (Bk == 32) {  // every lane has an item: combine the two halves of each block
+#pragma unroll
+        for (int k = 0; k < kMaxWidths; ++k) {
+          if (k < nw) {
+            const uint32_t ob = __shfl_xor_sync(0xffffffffu, best[k], 16);
+            const int oo = __shfl_xor_sync(0xffffffffu, boff[k], 16);
+            const bool take = ob > best[k] || (ob == best[k] && oo < boff[k]);
+            best[k] = take ? ob : best[k];
+            boff[k] = take ? oo : boff[k];
+          }
+        }
+      }
+      const int64_t jb = j0 + (int64_t)b * Bk;  // the block's first window sample
+      if (h == 0 && jb < nout) {
+        const int64_t blk = jb / Bk;
+#pragma unroll
+        for (int k = 0; k < kMaxWidths; ++k) {
+          if (k < nw) {
+            const int64_t idx = (rowk + k) * f.nblk + blk;
+            f.key[idx] = best[k];
+            f.off[idx] = (uint8_t)(best[k] ? boff[k] : 0);
+          }
         }
       }
     }
