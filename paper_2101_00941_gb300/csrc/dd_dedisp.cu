@@ -801,8 +801,8 @@ __device__ __forceinline__ bool tile_body(const TiledArgs& a, int bx, int by,
     if (t < ntr) {
       int32_t* yr = a.y + (int64_t)(trial0 + t) * a.y_stride;
       unsigned long long s1 = 0, lo = 0, hi = 0;
-#pragma unroll
       const bool store = !FUSED || f->keep_series;
+#pragma unroll
       for (int k = 0; k < KP; ++k) {
         const int64_t j = j0 + 2 * (lane + 32 * k);
         if (!store) {
