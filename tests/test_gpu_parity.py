@@ -7,6 +7,8 @@ ragged channel counts, every input kind (device, pinned, pageable), pipelined
 streams, an empty first window, and the full-size 4096-channel workload on
 sampled trials in the benchmark's launch configuration.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -402,3 +404,26 @@ def test_out_of_core_shape_from_pageable_memory_through_staging():
     trials = [sorted({0, r.n_trials - 1} | set(int(v) for v in rng.integers(0, r.n_trials, 2)))
               for r in w.ranges]
     assert check(w, x, [w.chunk_len, w.chunk_len], 2, kind="staged", trials=trials) >= 0
+
+
+def test_out_of_core_beam_in_the_benchmark_launch_configuration():
+    """The benchmark's default workload as it is launched: 8192 channels, DM 0-3000 x1..x16,
+    2^19-sample chunks over 4 streams, the plan's tile autotuner on, device-resident chunks.
+    Three chunks (the first window is shorter than a chunk by the overlap; the third is a full
+    window with history from both before it); two trials of every range, and the trial nearest
+    each injected pulse, bit-exact series and moments against the oracle, candidates per block.
+    About 10 minutes on the GPU machine, most of it the oracle's full-width decimation of 13 GB of
+    input, so it runs when DD_FULL_SIZE_TESTS=1 is set."""
+    if os.environ.get("DD_FULL_SIZE_TESTS") != "1":
+        pytest.skip("full-size out-of-core parity: set DD_FULL_SIZE_TESTS=1")
+    w = configs.out_of_core(nsamp=3 << 19)
+    x = w.generate(_arrivals(w))
+    trials = [sorted({0, r.n_trials - 1}) for r in w.ranges]
+    for p in w.pulses:
+        for ri, r in enumerate(w.ranges):
+            if r.dm_start <= p.dm < r.dm_start + r.n_trials * r.dm_step and p.t_ref < 3 << 19:
+                trials[ri] = sorted(set(trials[ri]) | {int((p.dm - r.dm_start) / r.dm_step)})
+    L = w.chunk_len
+    assert L == 1 << 19 and w.n_streams == 4
+    assert check(w, x, [L, L, L], 4, kind="device", trials=trials,
+                 flags=dd.DD_FLAG_AUTOTUNE) >= 0
