@@ -424,6 +424,16 @@ __device__ __forceinline__ double window_sqrt_var(const Moments& m, long long n)
   return sqrt(u128_to_f64(v_hi, v_lo));
 }
 
+// SNR >= thr  <=>  B >= (w*S1 + thr*den) / n. The bound keeps a margin of 2 + 1e-9 relative so
+// that rounding in this estimate can never reject a boxcar sum the exact test accepts; as a
+// uint32 bound on boxcar sums (< 2^31): at or below 0 every sum passes, above 2^32 - 1 none.
+__device__ __forceinline__ uint32_t window_bound(int w, long long s1, double thr, double den,
+                                                 long long n) {
+  const double t = ((double)w * (double)s1 + thr * den) / (double)n;
+  const double tl = t - 2.0 - 1e-9 * fabs(t);
+  return tl <= 0.0 ? 0u : (tl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(tl));
+}
+
 constexpr int kSpsThreads = 256;
 constexpr int kSpsSeg = kSpsThreads * 16;         // window samples per pass (16 per thread)
 constexpr int kSpsPad = 3;                        // aligns P[1 + hist + 4k] to 16 bytes
@@ -544,13 +554,7 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
       den[tid] = sqrt((double)w) * sq;
       ca[tid] = n;
       cb[tid] = (long long)w * s1;
-      // SNR >= thr  <=>  B >= (w*S1 + thr*den) / n; the bound keeps a margin of 2 + 1e-9
-      // relative so that rounding in this estimate can never reject a block the exact test
-      // accepts. As a uint32 bound on boxcar sums (< 2^31): at or below 0 every sum passes,
-      // above 2^32 - 1 none.
-      const double t = ((double)w * (double)s1 + thr * den[tid]) / (double)n;
-      const double tl = t - 2.0 - 1e-9 * fabs(t);
-      bthr[tid] = tl <= 0.0 ? 0u : (tl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(tl));
+      bthr[tid] = window_bound(w, s1, thr, den[tid], n);
     }
   } else if (tid < a.nw) {
     const WidthStats st = a.wst[(int64_t)i * a.nw + tid];
@@ -672,6 +676,7 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps(const SpsArgs a) {
 __global__ void __launch_bounds__(kSpsThreads) k_sps_fused(const SpsFusedArgs a) {
   __shared__ double den[kMaxWidths];
   __shared__ long long ca[kMaxWidths], cb[kMaxWidths];
+  __shared__ uint32_t kthr[kMaxWidths];
   const int32_t i = blockIdx.x;
   const int tid = threadIdx.x;
   const long long n = a.n;
@@ -679,14 +684,17 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps_fused(const SpsFusedArgs a)
   const Moments m = a.mom[i];
   const double sq = window_sqrt_var(m, n);
   if (sq == 0.0) return;  // constant series: no candidates
+  const double thr = (double)a.threshold;
   if (tid < a.nw) {
     const int w = a.wd[tid];
     den[tid] = sqrt((double)w) * sq;
     ca[tid] = n;
     cb[tid] = (long long)w * (long long)m.s1;
+    // a record can reach the threshold only if its sum passes k_sps's integer bound (key =
+    // sum + 1, so key > bound); the others are skipped before the FP64 SNR
+    kthr[tid] = window_bound(w, (long long)m.s1, thr, den[tid], n);
   }
   __syncthreads();
-  const double thr = (double)a.threshold;
   const int64_t row = (int64_t)i * a.nw;
   for (int64_t b = tid; b < a.nblk; b += kSpsThreads) {
     double bs = 0.0;
@@ -695,7 +703,7 @@ __global__ void __launch_bounds__(kSpsThreads) k_sps_fused(const SpsFusedArgs a)
     bool have = false;
     for (int k = 0; k < a.nw; ++k) {
       const uint32_t key = a.key[(row + k) * a.nblk + b];
-      if (key == 0) continue;
+      if (key == 0 || key <= kthr[k]) continue;  // no sample, or below the bound
       const long long best = (long long)(key - 1u);
       const long long jk = b * a.block + a.off[(row + k) * a.nblk + b];
       const long long num = ca[k] * best - cb[k];
