@@ -618,37 +618,48 @@ __device__ __forceinline__ void fused_search(const TiledArgs& a, const FusedArgs
 // Boxcars of a segment's first tile that start in the previous segment: per (boundary, trial),
 // width w, samples j < w - 1 of the tile, B = head[j] - tail[hist + j - w], merged into the
 // block's record (these samples precede every sample the fused pass saw in the block, so they
-// win ties). One CTA per (trial tile, boundary), one warp per trial.
+// win ties). CTA (4 x trial tile + quarter, boundary) takes 16 trials of the trial tile, one per
+// warp; a warp first copies its trial's head and tail into shared memory (independent loads, all
+// in flight), then works from there.
+constexpr int kEdgeTrials = 16;
+
 __global__ void __launch_bounds__(512) k_fused_edges(const __grid_constant__ TiledArgs a,
                                                      const __grid_constant__ FusedArgs f) {
-  const int bx = blockIdx.x, seg = blockIdx.y + 1;
+  extern __shared__ __align__(16) uint32_t edge_rows[];  // [16 warps][2][hist]
+  const int bx = blockIdx.x / 4, quarter = blockIdx.x % 4, seg = blockIdx.y + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t J = (int64_t)seg * f.seg_tiles * 512;
   if (J >= a.nout) return;
-  const int ntx = gridDim.x;
+  const int ntx = gridDim.x / 4;
   const int hist = f.hist, Bk = f.block;
-  const uint32_t* head = fused_edge(f, ntx, bx, seg);
-  const uint32_t* tail = fused_edge(f, ntx, bx, seg - 1) + kMaxTileTrials * (size_t)hist;
-  for (int t = warp; t < kMaxTileTrials; t += 16) {
-    const int trial = bx * kMaxTileTrials + t;
-    if (trial >= a.n_trials) break;
-    const uint32_t* hd = head + (size_t)t * hist;
-    const uint32_t* tl = tail + (size_t)t * hist;
-    for (int k = 0; k < f.nw; ++k) {
-      const int w = f.wd[k];
-      for (int jb = 0; jb < w - 1; jb += 32) {
-        const int jl = jb + lane;
-        const int64_t jg = J + jl;
-        const bool valid = jl < w - 1 && jg < a.nout;
-        const uint32_t key = valid ? hd[jl] + 1u - tl[hist + jl - w] : 0u;
-        int fo;
-        const uint32_t mx = group_max(key, Bk, lane, &fo);
-        if ((lane & (Bk - 1)) == 0 && jg < a.nout && mx != 0) {
-          const int64_t idx = ((int64_t)trial * f.nw + k) * f.nblk + jg / Bk;
-          if (mx >= f.key[idx]) {
-            f.key[idx] = mx;
-            f.off[idx] = (uint8_t)fo;
-          }
+  const int t = quarter * kEdgeTrials + warp;  // trial within the trial tile
+  const int trial = bx * kMaxTileTrials + t;
+  if (trial >= a.n_trials) return;  // warp-uniform; no barrier follows
+  const uint32_t* hd = fused_edge(f, ntx, bx, seg) + (size_t)t * hist;
+  const uint32_t* tl =
+      fused_edge(f, ntx, bx, seg - 1) + kMaxTileTrials * (size_t)hist + (size_t)t * hist;
+  uint32_t* H = edge_rows + (size_t)warp * 2 * hist;
+  uint32_t* T = H + hist;
+#pragma unroll 4
+  for (int i = lane; i < hist; i += 32) {
+    H[i] = __ldcg(hd + i);
+    T[i] = __ldcg(tl + i);
+  }
+  __syncwarp();
+  for (int k = 0; k < f.nw; ++k) {
+    const int w = f.wd[k];
+    for (int jb = 0; jb < w - 1; jb += 32) {
+      const int jl = jb + lane;
+      const int64_t jg = J + jl;
+      const bool valid = jl < w - 1 && jg < a.nout;
+      const uint32_t key = valid ? H[jl] + 1u - T[hist + jl - w] : 0u;
+      int fo;
+      const uint32_t mx = group_max(key, Bk, lane, &fo);
+      if ((lane & (Bk - 1)) == 0 && jg < a.nout && mx != 0) {
+        const int64_t idx = ((int64_t)trial * f.nw + k) * f.nblk + jg / Bk;
+        if (mx >= f.key[idx]) {
+          f.key[idx] = mx;
+          f.off[idx] = (uint8_t)fo;
         }
       }
     }
@@ -1351,6 +1362,10 @@ cudaError_t prepare_fused_t() {
 
 cudaError_t prepare_fused(int is_u16, int nstage, size_t smem) {
   if (smem > kSmemLimit) return cudaErrorInvalidValue;
+  const cudaError_t e = cudaFuncSetAttribute(k_fused_edges,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((512 / 32) * 2 * 512 * sizeof(uint32_t)));
+  if (e != cudaSuccess) return e;
   if (!is_u16 && nstage == 4) return prepare_fused_t<uint8_t, 4>();
   if (!is_u16 && nstage == 3) return prepare_fused_t<uint8_t, 3>();
   if (is_u16 && nstage == 4) return prepare_fused_t<uint16_t, 4>();
@@ -1391,7 +1406,8 @@ cudaError_t launch_fused(const TiledArgs& a, const FusedArgs& f, int is_u16, siz
   else return cudaErrorInvalidValue;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || f.nsegs < 2) return e;
-  k_fused_edges<<<dim3((unsigned)ntx, (unsigned)(f.nsegs - 1)), 512, 0, st>>>(a, f);
+  const size_t esmem = (size_t)(512 / 32) * 2 * f.hist * sizeof(uint32_t);
+  k_fused_edges<<<dim3((unsigned)ntx * 4, (unsigned)(f.nsegs - 1)), 512, esmem, st>>>(a, f);
   return cudaGetLastError();
 }
 
