@@ -44,6 +44,7 @@ UNIT = "DM-trial·samples/s"
 # DRAM bytes over algorithmic bytes of the dedispersion launches, from one ncu capture; valid only
 # for the kernel source it was taken on (its SHA-256 is stored beside the figures)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dedisp_dram_traffic.json")
+TRAFFIC_FILE_FUSED = os.path.join(ROOT, "profiles", "dedisp_fused_dram_traffic.json")
 DEDISP_SOURCE = os.path.join(ROOT, "paper_2101_00941_gb300", "csrc", "dd_dedisp.cu")
 
 
@@ -630,12 +631,12 @@ def launch_model(plan, w, O: int, T0: int, sizes):
     return tot, per
 
 
-def dram_traffic_ratio():
+def dram_traffic_ratio(path=TRAFFIC_FILE):
     """DRAM bytes (read + write) of the dedispersion launches over their algorithmic bytes, from
     the committed ncu capture, or None when the capture was taken on another revision of the
     kernel source (its SHA-256 is stored beside the figures)."""
     try:
-        with open(TRAFFIC_FILE) as fh:
+        with open(path) as fh:
             rec = json.load(fh)
         with open(DEDISP_SOURCE, "rb") as fh:
             sha = hashlib.sha256(fh.read()).hexdigest()
@@ -721,7 +722,7 @@ def main(args):
     dd_s = dd_ms * 1e-3
     achieved = tot["adds"] / dd_s if dd_s > 0 else None
     smem_wf = tot["smem_wavefronts"] + tot["copy_bytes"] / 128.0
-    ratio = None if nfused else dram_traffic_ratio()  # the record is of the plain kernel
+    ratio = dram_traffic_ratio(TRAFFIC_FILE_FUSED if nfused else TRAFFIC_FILE)
     per_range = []
     for r, (rms, rn) in enumerate(range_ms):
         p = per_solo[r]
@@ -769,7 +770,8 @@ def main(args):
             "traffic": ratio * tot["dram_bytes"] / dd_n if (ratio and dd_n) else None,
             "traffic_unit": "bytes per launch",
             "traffic_note": "measured DRAM bytes / algorithmic bytes of a committed ncu capture "
-                            "of the same kernel source (profiles/dedisp_dram_traffic.json) x the "
+                            "of the same kernel source (profiles/dedisp_dram_traffic.json, or "
+                            "dedisp_fused_dram_traffic.json for the fused search) x the "
                             "algorithmic bytes of the timed launches (dd_plan_model); null when "
                             "the kernel source has changed since the capture",
             "algorithmic_dram_bytes_per_launch": tot["dram_bytes"] / dd_n if dd_n else None,
