@@ -597,13 +597,15 @@ def peaks_workload(args):
     return 0
 
 
-def outputs_of_chunks(w, O: int, T0: int, sizes) -> int:
+def outputs_of_chunks(w, O: int, T0: int, sizes, input_equivalent: bool = False) -> int:
     """DM-trial*samples the library produces for chunks of `sizes` samples delivered from stream
-    position T0 on: range r outputs the decimated indices j with j*d_r in [T - O, T + n - O)."""
+    position T0 on: range r outputs the decimated indices j with j*d_r in [T - O, T + n - O).
+    With input_equivalent, each decimated output counts the d_r original samples it covers."""
     out, T = 0, T0
     for n in sizes:
         lo, hi = max(0, T - O), max(0, T + n - O)
-        out += sum(r.n_trials * (hi // r.decimation - lo // r.decimation) for r in w.ranges)
+        out += sum(r.n_trials * (hi // r.decimation - lo // r.decimation) *
+                   (r.decimation if input_equivalent else 1) for r in w.ranges)
         T += n
     return out
 
@@ -693,6 +695,7 @@ def main(args):
     T0 = args.warmup * w.nsamp  # stream position of the timed steps
     sizes = [L] * nchunks * args.steps
     outs = outputs_of_chunks(w, O, T0, sizes)
+    outs_in = outputs_of_chunks(w, O, T0, sizes, input_equivalent=True)
     tot, per = launch_model(plan, w, O, T0, sizes)
     lat = []
     ms_e2e, ncand_e2e, _, _, _ = time_steps(plan, hchunks, w, args.steps, args.warmup, barrier,
@@ -755,6 +758,10 @@ def main(args):
                    "l2": f"every chunk {L * w.nchans / 1e9:.1f} GB > L2 (no flush)",
                    "fused_search_ranges": nfused},
         "real_time_factor": obs / (ms * 1e-3 / args.steps),
+        "input_equivalent": {"value": outs_in * world / (ms * 1e-3), "unit": UNIT,
+                             "note": "the same steps counting each decimated output as the d_r "
+                                     "original samples it covers (sum over ranges of n_r x the "
+                                     "chunk window at the original sampling)"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": w.nsamp * w.nchans,
                 "d2h_bytes_per_step": int(ncand_e2e / args.steps * 32 + nchunks * 16),
                 "real_time_factor": obs / (ms_e2e * 1e-3 / args.steps),

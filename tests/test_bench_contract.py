@@ -52,6 +52,7 @@ def test_gpu_arm_line():
     assert d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 3 and d["gpu_launches"] > 0
     assert d["e2e"]["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == (2 << 19) * 8192
     assert "exposed_copy_ms_per_chunk" in d["e2e"] and "chunk_latency_ms" in d["e2e"]
+    assert d["input_equivalent"]["value"] > d["value"]  # decimated ranges count d_r samples
     r = d["roofline"]
     assert r["bound"] == "alu" and 0 < r["frac"] < 2 and r["peak"] > 0
     assert 0 < r["frac_smem"] < 1.5
@@ -88,3 +89,6 @@ def test_metric_counts_the_outputs_of_the_chunk_windows():
     # a continuing stream's step produces every range's full N / d_r outputs per trial
     assert bench.outputs_of_chunks(w, O, 3 * w.nsamp, sizes) == \
         sum(r.n_trials * (w.nsamp // r.decimation) for r in w.ranges)
+    # counted at the original sampling, every trial covers the whole N samples
+    assert bench.outputs_of_chunks(w, O, 3 * w.nsamp, sizes, input_equivalent=True) == \
+        w.n_trials * w.nsamp
