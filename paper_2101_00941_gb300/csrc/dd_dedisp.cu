@@ -75,8 +75,13 @@ struct ClsEntry {
   int32_t pad;
 };
 
+// Entry of trial t of a tile in GroupTab::zstart for a CTA of W warps with tpw trials per warp:
+// warp t mod W reads its trials t, t + W, ... as tpw consecutive entries.
+__host__ __device__ constexpr int trial_slot(int t, int W, int tpw) { return (t % W) * tpw + t / W; }
+
 struct GroupTab {
-  int16_t zstart[kMaxTileTrials];  // stage word offset of each trial's sequence (0: no trial)
+  int16_t zstart[kMaxTileTrials];  // stage word offset of each trial's sequence (0: no trial),
+                                   // warp-major: entry trial_slot(t) (a warp's trials contiguous)
   ClsEntry cls[kMaxCls];
   int32_t ncls, pad0, pad1, pad2;
 };
@@ -771,10 +776,19 @@ __device__ __forceinline__ bool tile_body(const TiledArgs& a, int bx, int by,
       const uint32_t* Zs = Zbuf + (size_t)(s & 1) * a.zcap + lane;
       const uint32_t* zp[kTPW];
       const uint32_t* zq[kTPW];
-#pragma unroll
-      for (int q = 0; q < kTPW; ++q) {
-        zp[q] = Zs + tc.g[0].zstart[warp + W * q];
-        zq[q] = Zs + tc.g[1].zstart[warp + W * q];
+      static_assert(kTPW == 4 || kTPW == 2, "a warp's offsets are one 8- or 4-byte load");
+      if constexpr (kTPW == 4) {
+        const uint2 e0 = *reinterpret_cast<const uint2*>(tc.g[0].zstart + warp * 4);
+        const uint2 e1 = *reinterpret_cast<const uint2*>(tc.g[1].zstart + warp * 4);
+        zp[0] = Zs + (e0.x & 0xFFFFu); zp[1] = Zs + (e0.x >> 16);
+        zp[2] = Zs + (e0.y & 0xFFFFu); zp[3] = Zs + (e0.y >> 16);
+        zq[0] = Zs + (e1.x & 0xFFFFu); zq[1] = Zs + (e1.x >> 16);
+        zq[2] = Zs + (e1.y & 0xFFFFu); zq[3] = Zs + (e1.y >> 16);
+      } else {
+        const uint32_t e0 = *reinterpret_cast<const uint32_t*>(tc.g[0].zstart + warp * 2);
+        const uint32_t e1 = *reinterpret_cast<const uint32_t*>(tc.g[1].zstart + warp * 2);
+        zp[0] = Zs + (e0 & 0xFFFFu); zp[1] = Zs + (e0 >> 16);
+        zq[0] = Zs + (e1 & 0xFFFFu); zq[1] = Zs + (e1 >> 16);
       }
       if (ng == kNG) {  // uniform; only the last stage may hold one group
 #pragma unroll
@@ -1016,7 +1030,7 @@ static void tiled_smem_work(TiledPlan& P, int ntiles, int nstages, int ngroups, 
       const StageTab& st = tabs[(size_t)ti * nstages + s];
       const int ng = std::min(kNG, ngroups - s * kNG);
       lsu += (int64_t)W * kTPW * KP * ng;             // accumulation words
-      lsu += (int64_t)W * kTPW * ng;                  // zstart entries
+      lsu += (int64_t)W * ng;                         // zstart entries (one load per group)
       lsu += W;                                       // nwork
       for (int w = 0; w < kWarps; ++w)
         for (int k = 0; k < st.nwork[w]; ++k) {
@@ -1122,7 +1136,8 @@ TiledPlan tiled_plan(const int32_t* tab, int ntr, int cpad, int decimation, int 
         }
         for (int i = 0; i < n; ++i) {
           const int p = cls_of[i], o = b[i] - cmin[p];
-          gt.zstart[i] = (int16_t)(zoff[p] + (o % 2) * (zlens[p] / 2) + o / 2);
+          gt.zstart[trial_slot(i, nt / 32, D / (nt / 32))] =
+              (int16_t)(zoff[p] + (o % 2) * (zlens[p] / 2) + o / 2);
         }
         gt.ncls = ncls;
       }
@@ -1231,7 +1246,7 @@ int64_t tiled_plan_check(const int32_t* tab, int ntr, int cpad, int decimation, 
         const int c0 = (s * kNG + gl) * kG;
         for (int p = 0; p < gt.ncls; ++p) bad += (gt.cls[p].zoff % 4) + (gt.cls[p].zlen % 4) != 0;
         for (int i = 0; i < n; ++i) {
-          const int z = gt.zstart[i];
+          const int z = gt.zstart[trial_slot(i, kWarps, D / kWarps)];
           int p = 0, o = -1;
           for (; p < gt.ncls; ++p) {
             const int zo = gt.cls[p].zoff, half = gt.cls[p].zlen / 2;
